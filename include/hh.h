@@ -1,0 +1,212 @@
+/*
+ * hh.h -- C ABI of the GB300 curved-ray heat-haze engine.
+ *
+ * The engine implements the rendering hot path of "Real-Time 3D Simulation of
+ * Heat-Induced Air Turbulence" (arXiv 2603.02048, Sec. 3.3): SPH particle
+ * densities are splatted onto a voxel grid (Sec. 3.3.1), mapped to a
+ * refractive-index volume by Gladstone-Dale with its gradient by finite
+ * differences (Eqs. 12-13), and one curved ray per pixel is integrated through
+ * it (Eqs. 14-16) with the curvature-adaptive step of Eqs. 17-18; the exit ray
+ * looks up a background (the stand-in for the paper's scene intersection).
+ *
+ * Conventions shared by every call
+ *  - Units are voxels. A grid of nx*ny*nz voxels covers the box
+ *    [0,nx] x [0,ny] x [0,nz]; voxel (i,j,k) has its centre at
+ *    (i+1/2, j+1/2, k+1/2). Dense arrays are x-fastest:
+ *    index = (k*ny + j)*nx + i.
+ *  - Pointers named *_dev are CUDA device pointers on the current device; the
+ *    caller owns them and keeps them alive until the work on `stream` ends.
+ *    hh_volume handles are owned by the library (free with hh_volume_free).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Every call only enqueues work on it and returns; results are
+ *    ready when the stream reaches that point. Calls that allocate or read
+ *    back host values say so.
+ *  - No call aborts, traps or prints. Each returns an hh_status; on failure
+ *    hh_last_error() holds a message for the calling thread.
+ *  - All arithmetic on the device is FP32 (storage may be FP16); nothing on
+ *    the device uses FP64.
+ */
+#ifndef HH_H_
+#define HH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HH_OK = 0,
+    HH_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is out of range */
+    HH_ERR_OOM = 2,         /* device memory (or a serving budget) is short  */
+    HH_ERR_CUDA = 3,        /* a CUDA runtime call failed                    */
+    HH_ERR_TIMEOUT = 4,     /* a bounded wait ran out                        */
+    HH_ERR_BUSY = 5,        /* the request is still running                  */
+    HH_ERR_CANCELLED = 6,   /* the request was cancelled                     */
+    HH_ERR_NOT_FOUND = 7    /* unknown ticket, frame or handle               */
+} hh_status;
+
+/* Storage of the {dn, grad n} volume. */
+typedef enum {
+    HH_STORE_FP32 = 0,       /* 4 x float per voxel, 16 B                     */
+    HH_STORE_FP16_SCALED = 1 /* 4 x half per voxel, 8 B: dn / s_n and g / s_g */
+} hh_storage;
+
+/* Integrator of the ray ODE (Eq. 15). */
+typedef enum {
+    HH_STEP_EULER_PAPER = 0, /* Eq. 16: w' = normalize(w + ds/n g_perp), C' = C + ds w' */
+    HH_STEP_RK4 = 1          /* classical RK4 of Eq. 15 in (C, w), w normalised per step  */
+} hh_stepper;
+
+/* Ray flag bits (hh_view_out.flags). */
+#define HH_FLAG_HIT 1u      /* the primary ray entered the volume box          */
+#define HH_FLAG_EXITED 2u   /* it left the box through the exit clip           */
+#define HH_FLAG_MAXSTEPS 4u /* it used max_steps steps without leaving the box */
+
+/* SPH particles, Sec. 3.1 Eq. 1 reduced to what the splat reads: n records of
+ * float4 {x, y, z, m} on the device, positions in voxel units. */
+typedef struct {
+    const float* xyzm_dev;
+    int64_t n;
+} hh_particles;
+
+/* Voxel grid of the refractive-index volume (Sec. 3.3.1, resolution R). */
+typedef struct {
+    int nx, ny, nz;  /* voxels per axis, each >= 2                            */
+    float h_kernel;  /* splat smoothing length h (voxels); support radius 2h  */
+    int storage;     /* hh_storage                                            */
+} hh_grid;
+
+/* Opaque library-owned volume: dn = n - 1 and grad n on the device. */
+typedef struct hh_volume_s* hh_volume;
+
+/* Pinhole camera. Pixel (x, y) has row 0 at the top; its ray passes through
+ * the pixel centre: d = normalize(f + (2(x+1/2)/W - 1) t (W/H) r
+ * + (1 - 2(y+1/2)/H) t u) with f = normalize(look_at - eye),
+ * r = normalize(f x up), u = r x f, t = tan(vfov/2). */
+typedef struct {
+    float eye[3], look_at[3], up[3];
+    float vfov_deg; /* vertical field of view in degrees, (0, 180) */
+    int width, height;
+} hh_camera;
+
+/* Step schedule (Sec. 3.3.3). adaptive != 0: ds = clamp(n theta_max /
+ * (|(I - w w^T) g| + eps), h_min, h_max) (Eq. 18, second form); otherwise
+ * ds = h_fixed (the fixed-step variant of Sec. 4.1). */
+typedef struct {
+    int stepper;      /* hh_stepper                                          */
+    int adaptive;     /* 0 or 1                                              */
+    float h_fixed;    /* > 0 when !adaptive                                  */
+    float h_min;      /* > 0 when adaptive                                   */
+    float h_max;      /* >= h_min when adaptive                              */
+    float theta_max;  /* >= 0, radians                                       */
+    float eps;        /* >= 0, per voxel                                     */
+    int max_steps;    /* >= 0 steps inside the box per ray                   */
+} hh_step_params;
+
+/* Equirectangular RGB8 background (device), row-major H x W x 3, row 0 at the
+ * +z pole. Colour of direction d: phi = atan2(d_y, d_x), theta = polar angle
+ * from +z, u = (phi/2pi + 1/2) W - 1/2, v = theta/pi H - 1/2, bilinear over
+ * texel centres, u wrapping, v clamped; value/255. */
+typedef struct {
+    const uint8_t* rgb8_dev;
+    int width, height; /* width >= 1, height >= 2 */
+} hh_background;
+
+/* Per-view outputs (device, caller-owned), pixel-major in row order. rgb is
+ * required (H*W*3 floats in [0,1]); the others may be NULL.
+ * exit_pos / exit_dir: H*W*3 floats (voxel units; a ray that misses the box
+ * reports the eye and its primary direction); steps: H*W int32; flags:
+ * H*W uint32 of HH_FLAG_* bits. */
+typedef struct {
+    float* rgb;
+    float* exit_pos;
+    float* exit_dir;
+    int32_t* steps;
+    uint32_t* flags;
+} hh_view_out;
+
+/* ---------------------------------------------------------------------- */
+/* Volume construction (Sec. 3.3.1, Eqs. 12-13)                            */
+/* ---------------------------------------------------------------------- */
+
+/* Splat alone (Sec. 3.3.1): rho_dev[v] = sum_p m_p W(|x_v - x_p|, h) at voxel
+ * centres, W the M4 cubic spline (support 2h). rho_dev holds nx*ny*nz floats
+ * and is overwritten; voxels outside the grid are dropped. Accumulation is
+ * FP32 with atomics, so the summation order (and the last bits) vary between
+ * runs. grid->storage is ignored. */
+hh_status hh_splat_density(const hh_particles* particles, const hh_grid* grid, float* rho_dev,
+                           void* stream);
+
+/* Gladstone-Dale + gradient (Eqs. 12-13) of a given density: dn = K_gd rho,
+ * g = grad dn by central differences inside and one-sided differences on the
+ * first/last voxel of each axis, stored as grid->storage. For FP16 storage
+ * the per-volume scales s_n = max|dn| / 16384 and s_g = max|g| / 16384 are
+ * computed on the device. Allocates the volume (cudaMalloc) and returns it in
+ * *out; the computation is enqueued on `stream`. */
+hh_status hh_volume_from_density(const float* rho_dev, const hh_grid* grid, float K_gd,
+                                 void* stream, hh_volume* out);
+
+/* Same with dn given directly (equivalent to K_gd = 1 on rho = dn). */
+hh_status hh_volume_from_dn(const float* dn_dev, const hh_grid* grid, void* stream,
+                            hh_volume* out);
+
+/* Splat + Gladstone-Dale + gradient in one call: the full volume build of
+ * Sec. 3.3.1. Allocates the volume and its density scratch (4 B/voxel, kept
+ * with the volume for hh_volume_rebuild) with cudaMalloc; the computation is
+ * enqueued on `stream`. */
+hh_status hh_build_index_field(const hh_particles* particles, const hh_grid* grid, float K_gd,
+                               void* stream, hh_volume* out);
+
+/* Rebuilds an existing volume in place from a new particle set (the next
+ * simulation frame): splat into the volume's density scratch, then Eqs.
+ * 12-13, with the volume's grid, h and storage. Allocates nothing when the
+ * volume came from hh_build_index_field; otherwise its first call allocates
+ * the density scratch (cudaMalloc). Work queued earlier on other streams that
+ * still reads the volume must be ordered before this call by the caller. */
+hh_status hh_volume_rebuild(hh_volume vol, const hh_particles* particles, float K_gd,
+                            void* stream);
+
+/* Writes the volume as the march reads it, dequantised to FP32, into dst_dev:
+ * nx*ny*nz*4 floats {dn, gx, gy, gz} per voxel (x fastest). */
+hh_status hh_volume_export(hh_volume vol, float* dst_dev, void* stream);
+
+/* Grid, FP16 scales (1 for FP32 storage) and device bytes of a volume.
+ * Synchronises `stream` to read the scales. Any output may be NULL. */
+hh_status hh_volume_info(hh_volume vol, hh_grid* grid, float* s_n, float* s_g, size_t* bytes,
+                         void* stream);
+
+/* Releases the volume (cudaFree; synchronises the device first). NULL is ok. */
+hh_status hh_volume_free(hh_volume vol);
+
+/* ---------------------------------------------------------------------- */
+/* Curved-ray tracing (Sec. 3.3.2-3.3.3, Eqs. 14-18)                       */
+/* ---------------------------------------------------------------------- */
+
+/* Renders n_cams views of one volume. For every pixel: pinhole ray, slab
+ * entry into the box, straight outside it; inside, per step k the volume is
+ * sampled trilinearly at C_k (lattice coordinate p - 1/2 clamped to the
+ * voxel centres), g_perp = (I - w w^T) g, ds by the schedule, then Eq. 16
+ * (EULER_PAPER) or RK4; when a step leaves the box the segment is clipped
+ * at the face and the ray leaves with the new direction. The colour is the
+ * background at the exit direction. outs[i] belongs to cams[i]. */
+hh_status hh_trace(hh_volume vol, const hh_camera* cams, int n_cams,
+                   const hh_step_params* params, const hh_background* bg,
+                   const hh_view_out* outs, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Diagnostics                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* hh_last_error(void);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t hh_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HH_H_ */

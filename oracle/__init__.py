@@ -103,6 +103,10 @@ def _load():
                       ctypes.c_int]
         lib.hho_trace_field.argtypes = [ctypes.POINTER(_Field), _D] + trace_args
         lib.hho_trace_grid.argtypes = [_D, ctypes.c_int, ctypes.c_int, ctypes.c_int] + trace_args
+        lib.hho_march_rays.argtypes = [ctypes.POINTER(_Field), _D, _D, _D, ctypes.c_int64,
+                                       ctypes.POINTER(_Params), _D, _D,
+                                       ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_uint32), ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -242,6 +246,28 @@ def march_ray(field: dict, box, C0, w0, params: dict, path_cap: int = 0) -> dict
     if path_cap > 0:
         out["path"] = path[: min(out["steps"], path_cap)]
     return out
+
+
+def march_rays(field: dict, box, C0: np.ndarray, w0: np.ndarray, params: dict,
+               nthreads: int = 1) -> dict:
+    """Marches many rays from given start points C0 (n, 3) and unit directions
+    w0 (n, 3); returns exit_pos, exit_dir, steps, flags per ray."""
+    holder = _FieldHolder(field)
+    box = _vec3(box)
+    C0 = np.ascontiguousarray(C0, dtype=np.float64).reshape(-1, 3)
+    w0 = np.ascontiguousarray(w0, dtype=np.float64).reshape(-1, 3)
+    n = C0.shape[0]
+    P = _params(params)
+    ep = np.zeros((n, 3))
+    ed = np.zeros((n, 3))
+    steps = np.zeros(n, dtype=np.int32)
+    flags = np.zeros(n, dtype=np.uint32)
+    _load().hho_march_rays(ctypes.byref(holder.f), _ptr(box, ctypes.c_double),
+                           _ptr(C0, ctypes.c_double), _ptr(w0, ctypes.c_double), n,
+                           ctypes.byref(P), _ptr(ep, ctypes.c_double), _ptr(ed, ctypes.c_double),
+                           _ptr(steps, ctypes.c_int32), _ptr(flags, ctypes.c_uint32),
+                           int(nthreads))
+    return {"exit_pos": ep, "exit_dir": ed, "steps": steps, "flags": flags}
 
 
 def _trace(fn, lead_args, cam, params, bg, pixels, nthreads):

@@ -626,3 +626,51 @@ int hho_trace_grid(const double* vol4, int nx, int ny, int nz, const hho_camera*
     return hho_trace_field(&F, box, cam, P, bg, bgW, bgH, pixels, n_pix, rgb, exit_pos, exit_dir,
                            steps, flags, nthreads);
 }
+
+/* ------------------------------------------------------------------------- */
+/* Many rays from given start states (same march, striped over threads)      */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    const hho_field* F;
+    const double* box;
+    const double* C0;
+    const double* w0;
+    const hho_params* P;
+    int64_t n;
+    double* exit_pos;
+    double* exit_dir;
+    int32_t* steps;
+    uint32_t* flags;
+    int thread, nthreads;
+} rays_job;
+
+static void* rays_worker(void* arg) {
+    const rays_job* J = (const rays_job*)arg;
+    for (int64_t i = J->thread; i < J->n; i += J->nthreads)
+        hho_march_ray(J->F, J->box, J->C0 + 3 * i, J->w0 + 3 * i, J->P, J->exit_pos + 3 * i,
+                      J->exit_dir + 3 * i, J->steps + i, J->flags + i, NULL, 0);
+    return NULL;
+}
+
+/* Marches n rays with start points C0[3n] and unit directions w0[3n]; the
+ * results are hho_march_ray's (no HIT flag is added). Returns 0. */
+int hho_march_rays(const hho_field* F, const double box[3], const double* C0, const double* w0,
+                   int64_t n, const hho_params* P, double* exit_pos, double* exit_dir,
+                   int32_t* steps, uint32_t* flags, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    rays_job jobs[256];
+    pthread_t tid[256];
+    for (int t = 0; t < nthreads; ++t) {
+        rays_job J = {F, box, C0, w0, P, n, exit_pos, exit_dir, steps, flags, t, nthreads};
+        jobs[t] = J;
+    }
+    if (nthreads == 1) {
+        rays_worker(&jobs[0]);
+        return 0;
+    }
+    for (int t = 0; t < nthreads; ++t) pthread_create(&tid[t], NULL, rays_worker, &jobs[t]);
+    for (int t = 0; t < nthreads; ++t) pthread_join(tid[t], NULL);
+    return 0;
+}

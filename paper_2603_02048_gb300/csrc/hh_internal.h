@@ -1,0 +1,47 @@
+// Internal declarations shared by the C-ABI layer (api.cpp) and the kernels.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+#include "hh.h"
+
+// FP16 storage maps the largest |value| of a channel group to this code, so
+// every value down to ~3.7e-9 of the maximum is a normal half.
+#define HH_FP16_CODE_MAX 16384.0f
+
+struct hh_volume_s {
+    int nx, ny, nz;
+    int storage;        // hh_storage
+    float h_kernel;
+    void* data;         // float4 (FP32) or ushort4 of halves (FP16) per voxel
+    size_t bytes;       // bytes of data
+    float* scales_dev;  // [2] = {s_n, s_g} on the device (1, 1 for FP32)
+    unsigned* max_dev;  // [2] = bit patterns of max|dn|, max|g| (FP16 build)
+    float* rho_dev;     // density scratch for particle builds (nullable)
+    int device;
+};
+
+namespace hh {
+
+extern std::atomic<uint64_t> g_launches;
+
+inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Kernel launchers. Each returns the launch status (cudaGetLastError()).
+cudaError_t launch_splat(const float4* xyzm, int64_t n, int nx, int ny, int nz, float h,
+                         float* rho, cudaStream_t s);
+
+cudaError_t launch_field(const float* rho, int nx, int ny, int nz, float K, hh_volume_s* vol,
+                         cudaStream_t s);
+
+cudaError_t launch_export(const hh_volume_s* vol, float4* dst, cudaStream_t s);
+
+cudaError_t launch_trace(const hh_volume_s* vol, const hh_camera& cam,
+                         const hh_step_params& P, const hh_background& bg,
+                         const hh_view_out& out, cudaStream_t s);
+
+}  // namespace hh

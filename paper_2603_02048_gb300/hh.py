@@ -1,0 +1,262 @@
+"""Thin ctypes binding of the C ABI in include/hh.h, with the same names.
+
+Only argument marshalling happens here: torch tensors are used as device
+buffers (their data pointers are passed through), the current torch CUDA
+stream is passed as the cudaStream_t, and every status is turned into an
+exception. All computation runs in the CUDA kernels of libhh.so. There is no
+CPU fallback: if the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libhh.so")
+
+HH_OK = 0
+STATUS_NAMES = {0: "HH_OK", 1: "HH_ERR_INVALID_ARG", 2: "HH_ERR_OOM", 3: "HH_ERR_CUDA",
+                4: "HH_ERR_TIMEOUT", 5: "HH_ERR_BUSY", 6: "HH_ERR_CANCELLED",
+                7: "HH_ERR_NOT_FOUND"}
+HH_STORE_FP32 = 0
+HH_STORE_FP16_SCALED = 1
+HH_STEP_EULER_PAPER = 0
+HH_STEP_RK4 = 1
+HH_FLAG_HIT = 1
+HH_FLAG_EXITED = 2
+HH_FLAG_MAXSTEPS = 4
+
+STORAGES = {"fp32": HH_STORE_FP32, "fp16": HH_STORE_FP16_SCALED}
+STEPPERS = {"euler": HH_STEP_EULER_PAPER, "rk4": HH_STEP_RK4}
+
+
+class HHError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class hh_particles(ctypes.Structure):
+    _fields_ = [("xyzm_dev", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class hh_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("h_kernel", ctypes.c_float), ("storage", ctypes.c_int)]
+
+
+class hh_camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("look_at", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("vfov_deg", ctypes.c_float),
+                ("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+class hh_step_params(ctypes.Structure):
+    _fields_ = [("stepper", ctypes.c_int), ("adaptive", ctypes.c_int),
+                ("h_fixed", ctypes.c_float), ("h_min", ctypes.c_float),
+                ("h_max", ctypes.c_float), ("theta_max", ctypes.c_float),
+                ("eps", ctypes.c_float), ("max_steps", ctypes.c_int)]
+
+
+class hh_background(ctypes.Structure):
+    _fields_ = [("rgb8_dev", ctypes.c_void_p), ("width", ctypes.c_int),
+                ("height", ctypes.c_int)]
+
+
+class hh_view_out(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("exit_pos", ctypes.c_void_p),
+                ("exit_dir", ctypes.c_void_p), ("steps", ctypes.c_void_p),
+                ("flags", ctypes.c_void_p)]
+
+
+# Every symbol include/hh.h declares, with (restype, argtypes).
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "hh_splat_density": (ctypes.c_int, [ctypes.POINTER(hh_particles), ctypes.POINTER(hh_grid),
+                                        _P, _P]),
+    "hh_volume_from_density": (ctypes.c_int, [_P, ctypes.POINTER(hh_grid), ctypes.c_float, _P,
+                                              ctypes.POINTER(_P)]),
+    "hh_volume_from_dn": (ctypes.c_int, [_P, ctypes.POINTER(hh_grid), _P, ctypes.POINTER(_P)]),
+    "hh_build_index_field": (ctypes.c_int, [ctypes.POINTER(hh_particles),
+                                            ctypes.POINTER(hh_grid), ctypes.c_float, _P,
+                                            ctypes.POINTER(_P)]),
+    "hh_volume_rebuild": (ctypes.c_int, [_P, ctypes.POINTER(hh_particles), ctypes.c_float, _P]),
+    "hh_volume_export": (ctypes.c_int, [_P, _P, _P]),
+    "hh_volume_info": (ctypes.c_int, [_P, ctypes.POINTER(hh_grid),
+                                      ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_size_t), _P]),
+    "hh_volume_free": (ctypes.c_int, [_P]),
+    "hh_trace": (ctypes.c_int, [_P, ctypes.POINTER(hh_camera), ctypes.c_int,
+                                ctypes.POINTER(hh_step_params), ctypes.POINTER(hh_background),
+                                ctypes.POINTER(hh_view_out), _P]),
+    "hh_last_error": (ctypes.c_char_p, []),
+    "hh_kernel_launch_count": (ctypes.c_uint64, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libhh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; build it with "
+                               "python -m paper_2603_02048_gb300.build")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != HH_OK:
+        raise HHError(status, load().hh_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# --------------------------------------------------------------------------- #
+# marshalling helpers
+# --------------------------------------------------------------------------- #
+def make_grid(dims, h_kernel: float = 2.0, storage: str = "fp32") -> hh_grid:
+    nx, ny, nz = (int(d) for d in dims)
+    return hh_grid(nx, ny, nz, float(h_kernel), STORAGES[storage])
+
+
+def make_camera(cam: dict) -> hh_camera:
+    c = hh_camera()
+    c.eye[:] = [float(v) for v in cam["eye"]]
+    c.look_at[:] = [float(v) for v in cam["look_at"]]
+    c.up[:] = [float(v) for v in cam["up"]]
+    c.vfov_deg = float(cam["vfov_deg"])
+    c.width = int(cam["width"])
+    c.height = int(cam["height"])
+    return c
+
+
+def make_params(p: dict) -> hh_step_params:
+    return hh_step_params(STEPPERS[p.get("stepper", "euler")], int(bool(p.get("adaptive"))),
+                          float(p.get("h_fixed", 0.5)), float(p.get("h_min", 0.125)),
+                          float(p.get("h_max", 2.0)), float(p.get("theta_max", 3e-3)),
+                          float(p.get("eps", 1e-6)), int(p["max_steps"]))
+
+
+class Volume:
+    """Owns an hh_volume handle; freed on close() or garbage collection."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(load().hh_volume_free(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle is not None and self.handle.value:
+                load().hh_volume_free(self.handle)
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------- #
+# the C-ABI calls, same names
+# --------------------------------------------------------------------------- #
+def hh_splat_density(xyzm, grid: hh_grid, rho, stream=None):
+    """Splat particles (n, 4) float32 CUDA tensor into rho (nz*ny*nx floats)."""
+    parts = hh_particles(_ptr(xyzm), int(xyzm.shape[0]))
+    _check(load().hh_splat_density(ctypes.byref(parts), ctypes.byref(grid), _ptr(rho),
+                                   _stream(stream)))
+
+
+def hh_volume_from_density(rho, grid: hh_grid, K_gd: float, stream=None) -> Volume:
+    out = ctypes.c_void_p()
+    _check(load().hh_volume_from_density(_ptr(rho), ctypes.byref(grid), float(K_gd),
+                                         _stream(stream), ctypes.byref(out)))
+    return Volume(out)
+
+
+def hh_volume_from_dn(dn, grid: hh_grid, stream=None) -> Volume:
+    out = ctypes.c_void_p()
+    _check(load().hh_volume_from_dn(_ptr(dn), ctypes.byref(grid), _stream(stream),
+                                    ctypes.byref(out)))
+    return Volume(out)
+
+
+def hh_build_index_field(xyzm, grid: hh_grid, K_gd: float, stream=None) -> Volume:
+    parts = hh_particles(_ptr(xyzm), int(xyzm.shape[0]))
+    out = ctypes.c_void_p()
+    _check(load().hh_build_index_field(ctypes.byref(parts), ctypes.byref(grid), float(K_gd),
+                                       _stream(stream), ctypes.byref(out)))
+    return Volume(out)
+
+
+def hh_volume_rebuild(vol: Volume, xyzm, K_gd: float, stream=None):
+    parts = hh_particles(_ptr(xyzm), int(xyzm.shape[0]))
+    _check(load().hh_volume_rebuild(vol.handle, ctypes.byref(parts), float(K_gd),
+                                    _stream(stream)))
+
+
+def hh_volume_export(vol: Volume, dst, stream=None):
+    _check(load().hh_volume_export(vol.handle, _ptr(dst), _stream(stream)))
+
+
+def hh_volume_info(vol: Volume, stream=None) -> dict:
+    g = hh_grid()
+    s_n = ctypes.c_float()
+    s_g = ctypes.c_float()
+    nbytes = ctypes.c_size_t()
+    _check(load().hh_volume_info(vol.handle, ctypes.byref(g), ctypes.byref(s_n),
+                                 ctypes.byref(s_g), ctypes.byref(nbytes), _stream(stream)))
+    return {"dims": (g.nx, g.ny, g.nz), "h_kernel": g.h_kernel, "storage": g.storage,
+            "s_n": s_n.value, "s_g": s_g.value, "bytes": nbytes.value}
+
+
+def hh_volume_free(vol: Volume):
+    vol.close()
+
+
+def hh_trace(vol: Volume, cams, params, bg, outs, stream=None):
+    """cams: list of camera dicts or hh_camera; params: dict or hh_step_params;
+    bg: (H, W, 3) uint8 CUDA tensor; outs: list of dicts with CUDA tensors
+    'rgb' (required) and optional 'exit_pos', 'exit_dir', 'steps', 'flags'."""
+    n = len(cams)
+    c_cams = (hh_camera * max(n, 1))(*[c if isinstance(c, hh_camera) else make_camera(c)
+                                       for c in cams])
+    c_outs = (hh_view_out * max(n, 1))(*[
+        hh_view_out(_ptr(o["rgb"]), _ptr(o.get("exit_pos")), _ptr(o.get("exit_dir")),
+                    _ptr(o.get("steps")), _ptr(o.get("flags"))) for o in outs])
+    P = params if isinstance(params, hh_step_params) else make_params(params)
+    B = hh_background(_ptr(bg), int(bg.shape[1]), int(bg.shape[0]))
+    _check(load().hh_trace(vol.handle, c_cams, n, ctypes.byref(P), ctypes.byref(B), c_outs,
+                           _stream(stream)))
+
+
+def hh_last_error() -> str:
+    return load().hh_last_error().decode()
+
+
+def hh_kernel_launch_count() -> int:
+    return int(load().hh_kernel_launch_count())

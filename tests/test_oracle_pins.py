@@ -535,3 +535,19 @@ def test_trace_pixel_subset_and_threads_agree(oracle_lib):
     part = oracle_lib.trace_grid(vol, cam, P, bg, pixels=sub, nthreads=3)
     for k in ("rgb", "exit_pos", "exit_dir", "steps", "flags"):
         np.testing.assert_array_equal(part[k], full[k][sub])
+
+
+def test_march_rays_equals_single_rays(oracle_lib):
+    """The batched march is the single-ray march, ray by ray."""
+    r = np.random.default_rng(4)
+    C0 = np.c_[np.zeros(7), r.uniform(10, 54, size=(7, 2))]
+    w0 = np.c_[np.ones(7), r.uniform(-0.3, 0.3, size=(7, 2))]
+    w0 /= np.linalg.norm(w0, axis=1, keepdims=True)
+    P = {"stepper": "rk4", "adaptive": True, "h_min": 0.05, "h_max": 1.0, "theta_max": 1e-3,
+         "eps": 1e-6, "max_steps": 100000}
+    many = oracle_lib.march_rays(LUNE, BOX, C0, w0, P, nthreads=3)
+    for i in range(7):
+        one = oracle_lib.march_ray(LUNE, BOX, C0[i], w0[i], P)
+        np.testing.assert_array_equal(many["exit_pos"][i], one["exit_pos"])
+        np.testing.assert_array_equal(many["exit_dir"][i], one["exit_dir"])
+        assert many["steps"][i] == one["steps"] and many["flags"][i] == one["flags"]
