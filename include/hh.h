@@ -168,6 +168,28 @@ hh_status hh_build_index_field(const hh_particles* particles, const hh_grid* gri
 hh_status hh_volume_rebuild(hh_volume vol, const hh_particles* particles, float K_gd,
                             void* stream);
 
+/* Allocation-free volume build (no counterpart in the paper: it is a service
+ * for callers that cannot allocate device memory -- a host application that
+ * owns the whole device-memory budget and forbids libraries from allocating,
+ * or a real-time frame loop that must not pay cudaMalloc's implicit device
+ * synchronisation and unbounded latency). Same computation as
+ * hh_build_index_field with FP32 storage, but the density grid lives in a
+ * fixed device array compiled into the library (8 MiB, held on every device
+ * that loads the library until the process exits) and the result is written
+ * to the caller's vol4_dev: nx*ny*nz*4 floats {dn, gx, gy, gz} per voxel,
+ * x fastest (the hh_volume_export layout), 16-byte aligned.
+ * - Calls no cudaMalloc, cudaFree or other allocating routine.
+ * - nx*ny*nz must be at most 2,097,152 (e.g. 128^3); larger grids and
+ *   grid->storage != HH_STORE_FP32 return HH_ERR_INVALID_ARG.
+ * - The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ * - Every call on a device shares the one array and clears it first: calls
+ *   whose work overlaps on the GPU (other streams, other host threads) race
+ *   and corrupt each other's result; order them. */
+hh_status hh_build_index_field_noalloc(const hh_particles* particles, const hh_grid* grid,
+                                       float K_gd, float* vol4_dev, void* stream);
+
 /* Writes the volume as the march reads it, dequantised to FP32, into dst_dev:
  * nx*ny*nz*4 floats {dn, gx, gy, gz} per voxel (x fastest). */
 hh_status hh_volume_export(hh_volume vol, float* dst_dev, void* stream);

@@ -13,8 +13,6 @@ namespace hh {
 
 std::atomic<uint64_t> g_launches{0};
 
-namespace {
-
 thread_local std::string t_last_error;
 
 hh_status fail(hh_status st, const char* fmt, ...) {
@@ -37,6 +35,8 @@ hh_status ok() {
     t_last_error.clear();
     return HH_OK;
 }
+
+namespace {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 

@@ -31,6 +31,12 @@ extern std::atomic<uint64_t> g_launches;
 
 inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Error reporting shared by the C-ABI entry points (defined in api.cpp): set
+// the calling thread's hh_last_error() message and return the status.
+hh_status fail(hh_status st, const char* fmt, ...);
+hh_status cuda_fail(cudaError_t e, const char* what);
+hh_status ok();
+
 // Kernel launchers. Each returns the launch status (cudaGetLastError()).
 cudaError_t launch_splat(const float4* xyzm, int64_t n, int nx, int ny, int nz, float h,
                          float* rho, cudaStream_t s);

@@ -81,6 +81,9 @@ SIGNATURES = {
                                             ctypes.POINTER(hh_grid), ctypes.c_float, _P,
                                             ctypes.POINTER(_P)]),
     "hh_volume_rebuild": (ctypes.c_int, [_P, ctypes.POINTER(hh_particles), ctypes.c_float, _P]),
+    "hh_build_index_field_noalloc": (ctypes.c_int, [ctypes.POINTER(hh_particles),
+                                                    ctypes.POINTER(hh_grid), ctypes.c_float, _P,
+                                                    _P]),
     "hh_volume_export": (ctypes.c_int, [_P, _P, _P]),
     "hh_volume_info": (ctypes.c_int, [_P, ctypes.POINTER(hh_grid),
                                       ctypes.POINTER(ctypes.c_float),
@@ -217,6 +220,13 @@ def hh_volume_rebuild(vol: Volume, xyzm, K_gd: float, stream=None):
     parts = hh_particles(_ptr(xyzm), int(xyzm.shape[0]))
     _check(load().hh_volume_rebuild(vol.handle, ctypes.byref(parts), float(K_gd),
                                     _stream(stream)))
+
+
+def hh_build_index_field_noalloc(xyzm, grid: hh_grid, K_gd: float, vol4, stream=None):
+    """Allocation-free FP32 build into the caller's vol4 (nz*ny*nx*4 floats)."""
+    parts = hh_particles(_ptr(xyzm), int(xyzm.shape[0]))
+    _check(load().hh_build_index_field_noalloc(ctypes.byref(parts), ctypes.byref(grid),
+                                               float(K_gd), _ptr(vol4), _stream(stream)))
 
 
 def hh_volume_export(vol: Volume, dst, stream=None):
