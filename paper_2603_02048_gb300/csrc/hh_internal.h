@@ -13,12 +13,32 @@
 // every value down to ~3.7e-9 of the maximum is a normal half.
 #define HH_FP16_CODE_MAX 16384.0f
 
+// Volume layouts.
+//  LINEAR: x fastest, index (k*ny + j)*nx + i (the export / interchange layout).
+//  BRICK2: 2x2x2 micro-bricks. Brick (X,Y,Z) = (i>>1, j>>1, k>>1) in x-fastest
+//          order over ceil(n/2) bricks per axis; inside a brick the voxel sits
+//          at slot (i&1) | (j&1)<<1 | (k&1)<<2. One FP32 brick is one 128-byte
+//          line, and the eight corners of any trilinear cell occupy eight
+//          different slots, i.e. eight different 16-byte L1 bank groups, so a
+//          warp's corner loads spread over all banks whatever the view
+//          direction (the linear layout puts every y/z neighbour of a
+//          power-of-two grid into the same bank group).
+enum { HH_LAYOUT_LINEAR = 0, HH_LAYOUT_BRICK2 = 1 };
+
+__host__ __device__ __forceinline__ unsigned brick2_offset(unsigned i, unsigned j, unsigned k,
+                                                           unsigned bx, unsigned bxy) {
+    return (((k >> 1) * bxy + (j >> 1) * bx + (i >> 1)) << 3) | ((k & 1u) << 2) |
+           ((j & 1u) << 1) | (i & 1u);
+}
+
 struct hh_volume_s {
     int nx, ny, nz;
     int storage;        // hh_storage
+    int layout;         // HH_LAYOUT_*
+    unsigned bx, bxy;   // BRICK2: bricks along x, bricks per xy plane
     float h_kernel;
     void* data;         // float4 (FP32) or ushort4 of halves (FP16) per voxel
-    size_t bytes;       // bytes of data
+    size_t bytes;       // bytes of data (BRICK2 pads every axis to even)
     float* scales_dev;  // [2] = {s_n, s_g} on the device (1, 1 for FP32)
     unsigned* max_dev;  // [2] = bit patterns of max|dn|, max|g| (FP16 build)
     float* rho_dev;     // density scratch for particle builds (nullable)

@@ -11,12 +11,21 @@
 //    with r - 1 = -e / (s (1 + s)), e = 2 w_ref.d1 + |d1|^2, s = sqrt(1 + e),
 //    so rounding never touches the O(1) part of w and the deflection keeps
 //    full relative precision over thousands of steps.
-//  - The position is a compensated pair (hi + lo): each increment is added
-//    with an error-free TwoSum and the rounding error is kept in lo.
+//  - The position is a compensated pair (hi + lo): hi carries a power-of-two
+//    bias B (hi = position + B, B above every coordinate and step), so every
+//    increment is smaller than hi and Fast2Sum is error-free; its rounding
+//    error goes to lo. The position proper is (hi - B) + lo, where hi - B is
+//    exact (Sterbenz).
+//  - Divisions and square roots whose operands are far from any cancellation
+//    (ds / n, n theta / (|g_perp| + eps), the renormalisation term, |g_perp|)
+//    use the approximate hardware forms (relative error ~1e-7, harmless next
+//    to the 1e-6 rad tolerance: they perturb steps, not the path).
 //
 // Layout: a block of 128 threads covers a 16x8 pixel tile; each warp an 8x4
 // sub-tile, so the rays of a warp stay close in the volume and their eight
-// corner fetches per step share cache lines in L1.
+// corner fetches per step share cache lines in L1. The volume is stored in
+// 2x2x2 micro-bricks (BRICK2), which spreads the distinct voxels of a warp's
+// corner load over all L1 bank groups.
 #include "hh_internal.h"
 
 namespace hh {
@@ -28,6 +37,9 @@ struct TraceArgs {
     const void* vol;
     const float* scales;
     int nx, ny, nz;
+    unsigned bx, bxy;   // BRICK2 bricks along x and per xy plane
+    unsigned by8, bz8;  // BRICK2 strides (in elements) of one brick step in y and z
+    float bias;         // power of two above every coordinate and step
     float3 eye, look, up;
     float vfov_deg;
     int W, H;
@@ -69,11 +81,17 @@ __device__ __forceinline__ float3 fma3(float s, float3 b, float3 a) {
 }
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
-// Error-free sum: s + e == a + b exactly (Knuth's TwoSum, no FMA involved).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+// Error-free sum for |a| >= |b| (Dekker's Fast2Sum): s + e == a + b exactly.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// Hardware approximate square root (PTX sqrt.approx.f32, ~1 ulp).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // Lattice cell and weight along one axis: u = p - 1/2 clamped to [0, n-1],
@@ -84,10 +102,10 @@ __device__ __forceinline__ void axis_cell(float p, int n, int& i0, float& f) {
     f = u - static_cast<float>(i0);
 }
 
-__device__ __forceinline__ float4 ld_fp32(const float4* __restrict__ v, size_t i) {
+__device__ __forceinline__ float4 ld_fp32(const float4* __restrict__ v, unsigned i) {
     return __ldg(v + i);
 }
-__device__ __forceinline__ float4 ld_fp16(const ushort4* __restrict__ v, size_t i) {
+__device__ __forceinline__ float4 ld_fp16(const ushort4* __restrict__ v, unsigned i) {
     const uint2 raw = __ldg(reinterpret_cast<const uint2*>(v) + i);
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
@@ -108,34 +126,60 @@ __device__ __forceinline__ Sample fetch(const TraceArgs& A, float3 p) {
     axis_cell(p.x, A.nx, ix, fx);
     axis_cell(p.y, A.ny, iy, fy);
     axis_cell(p.z, A.nz, iz, fz);
-    const size_t sy = static_cast<size_t>(A.nx);
-    const size_t sz = sy * A.ny;
-    const size_t b = static_cast<size_t>(iz) * sz + static_cast<size_t>(iy) * sy + ix;
+    // BRICK2 element of corner (ix, iy, iz), then the steps to the other
+    // corners: +1 in x stays in the brick (slot +1) when ix is even, else it
+    // moves to the next brick (slot -1, brick +1: +7); likewise y (+2 or
+    // by8 - 2) and z (+4 or bz8 - 4).
+    const unsigned b = brick2_offset(ix, iy, iz, A.bx, A.bxy);
+    const unsigned dx = (ix & 1) ? 7u : 1u;
+    const unsigned dy = (iy & 1) ? A.by8 - 2u : 2u;
+    const unsigned dz = (iz & 1) ? A.bz8 - 4u : 4u;
+    const unsigned b010 = b + dy, b001 = b + dz, b011 = b001 + dy;
     float4 v000, v100, v010, v110, v001, v101, v011, v111;
     if (STORAGE == HH_STORE_FP32) {
         const float4* V = static_cast<const float4*>(A.vol);
         v000 = ld_fp32(V, b);
-        v100 = ld_fp32(V, b + 1);
-        v010 = ld_fp32(V, b + sy);
-        v110 = ld_fp32(V, b + sy + 1);
-        v001 = ld_fp32(V, b + sz);
-        v101 = ld_fp32(V, b + sz + 1);
-        v011 = ld_fp32(V, b + sz + sy);
-        v111 = ld_fp32(V, b + sz + sy + 1);
+        v100 = ld_fp32(V, b + dx);
+        v010 = ld_fp32(V, b010);
+        v110 = ld_fp32(V, b010 + dx);
+        v001 = ld_fp32(V, b001);
+        v101 = ld_fp32(V, b001 + dx);
+        v011 = ld_fp32(V, b011);
+        v111 = ld_fp32(V, b011 + dx);
     } else {
         const ushort4* V = static_cast<const ushort4*>(A.vol);
         v000 = ld_fp16(V, b);
-        v100 = ld_fp16(V, b + 1);
-        v010 = ld_fp16(V, b + sy);
-        v110 = ld_fp16(V, b + sy + 1);
-        v001 = ld_fp16(V, b + sz);
-        v101 = ld_fp16(V, b + sz + 1);
-        v011 = ld_fp16(V, b + sz + sy);
-        v111 = ld_fp16(V, b + sz + sy + 1);
+        v100 = ld_fp16(V, b + dx);
+        v010 = ld_fp16(V, b010);
+        v110 = ld_fp16(V, b010 + dx);
+        v001 = ld_fp16(V, b001);
+        v101 = ld_fp16(V, b001 + dx);
+        v011 = ld_fp16(V, b011);
+        v111 = ld_fp16(V, b011 + dx);
     }
-    const float4 c0 = lerp4(lerp4(v000, v100, fx), lerp4(v010, v110, fx), fy);
-    const float4 c1 = lerp4(lerp4(v001, v101, fx), lerp4(v011, v111, fx), fy);
-    const float4 c = lerp4(c0, c1, fz);
+    // the standard 8-corner weights
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    const float w00 = gy * gz, w10 = fy * gz, w01 = gy * fz, w11 = fy * fz;
+    const float w000 = gx * w00, w100 = fx * w00, w010 = gx * w10, w110 = fx * w10;
+    const float w001 = gx * w01, w101 = fx * w01, w011 = gx * w11, w111 = fx * w11;
+    float4 c;
+    c.x = w000 * v000.x;
+    c.y = w000 * v000.y;
+    c.z = w000 * v000.z;
+    c.w = w000 * v000.w;
+#define HH_ACC(W, V)              \
+    c.x = fmaf(W, V.x, c.x);      \
+    c.y = fmaf(W, V.y, c.y);      \
+    c.z = fmaf(W, V.z, c.z);      \
+    c.w = fmaf(W, V.w, c.w);
+    HH_ACC(w100, v100)
+    HH_ACC(w010, v010)
+    HH_ACC(w110, v110)
+    HH_ACC(w001, v001)
+    HH_ACC(w101, v101)
+    HH_ACC(w011, v011)
+    HH_ACC(w111, v111)
+#undef HH_ACC
     Sample s;
     if (STORAGE == HH_STORE_FP32) {
         s.dn = c.x;
@@ -156,15 +200,15 @@ __device__ __forceinline__ Sample fetch(const TraceArgs& A, float3 p) {
 template <bool ADAPTIVE>
 __device__ __forceinline__ float step_length(const TraceArgs& A, float n, float gperp_norm) {
     if (!ADAPTIVE) return A.h_fixed;
-    return fminf(fmaxf(n * A.theta / (gperp_norm + A.eps), A.h_min), A.h_max);
+    return fminf(fmaxf(__fdividef(n * A.theta, gperp_norm + A.eps), A.h_min), A.h_max);
 }
 
 // Eq. 16's normalize, in deflection form: returns d' with w_ref + d' the unit
 // vector along w_ref + d1 (taking |w_ref| = 1).
 __device__ __forceinline__ float3 renormalize(float3 wr, float3 d1) {
     const float e = 2.0f * dot(wr, d1) + dot(d1, d1);
-    const float s = sqrtf(1.0f + e);
-    const float rm1 = -e / (s * (1.0f + s));
+    const float s = sqrt_approx(1.0f + e);
+    const float rm1 = __fdividef(-e, s * (1.0f + s));
     return fma3(rm1, wr + d1, d1);
 }
 
@@ -259,12 +303,12 @@ __device__ __forceinline__ float3 perp_rate(const TraceArgs& A, float3 p, float3
     n = 1.0f + s.dn;
     const float3 g = make_float3(s.gx, s.gy, s.gz);
     const float3 gp = fma3(-dot(w, g), w, g);
-    gperp_norm = sqrtf(dot(gp, gp));
+    gperp_norm = sqrt_approx(dot(gp, gp));
     return gp;
 }
 
 template <int STORAGE, int STEPPER, bool ADAPTIVE>
-__global__ void __launch_bounds__(128) march_kernel(const TraceArgs A) {
+__global__ void __launch_bounds__(128, (STEPPER == HH_STEP_RK4) ? 6 : 8) march_kernel(const TraceArgs A) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
@@ -277,11 +321,16 @@ __global__ void __launch_bounds__(128) march_kernel(const TraceArgs A) {
     float t_in;
     if (slab(A, A.eye, wr, t_in)) {
         flags = HH_FLAG_HIT;
-        float3 hi = fma3(fmaxf(t_in, 0.0f), wr, A.eye);
-        float3 lo = make_float3(0.0f, 0.0f, 0.0f);
+        // position = (hi - B) + lo with hi = position + B (see the header)
+        const float B = A.bias;
+        const float3 entry = fma3(fmaxf(t_in, 0.0f), wr, A.eye);
+        float3 hi, lo;
+        fast_two_sum(B, entry.x, hi.x, lo.x);
+        fast_two_sum(B, entry.y, hi.y, lo.y);
+        fast_two_sum(B, entry.z, hi.z, lo.z);
         float3 d = make_float3(0.0f, 0.0f, 0.0f);
         for (k = 0; k < A.max_steps; ++k) {
-            const float3 C = hi + lo;
+            const float3 C = make_float3((hi.x - B) + lo.x, (hi.y - B) + lo.y, (hi.z - B) + lo.z);
             float ds;
             float3 dnew, inc;
             if (STEPPER == HH_STEP_RK4) {
@@ -290,19 +339,19 @@ __global__ void __launch_bounds__(128) march_kernel(const TraceArgs A) {
                 const float3 gp1 = perp_rate<STORAGE, ADAPTIVE>(A, C, w1, n1, gpn);
                 ds = step_length<ADAPTIVE>(A, n1, gpn);
                 const float hds = 0.5f * ds;
-                const float3 k1 = (1.0f / n1) * gp1;
+                const float3 k1 = __fdividef(1.0f, n1) * gp1;
                 const float3 d2 = fma3(hds, k1, d);
                 const float3 w2 = wr + d2;
                 const float3 gp2 = perp_rate<STORAGE, ADAPTIVE>(A, fma3(hds, w1, C), w2, n2, unused);
-                const float3 k2 = (1.0f / n2) * gp2;
+                const float3 k2 = __fdividef(1.0f, n2) * gp2;
                 const float3 d3 = fma3(hds, k2, d);
                 const float3 w3 = wr + d3;
                 const float3 gp3 = perp_rate<STORAGE, ADAPTIVE>(A, fma3(hds, w2, C), w3, n3, unused);
-                const float3 k3 = (1.0f / n3) * gp3;
+                const float3 k3 = __fdividef(1.0f, n3) * gp3;
                 const float3 d4 = fma3(ds, k3, d);
                 const float3 w4 = wr + d4;
                 const float3 gp4 = perp_rate<STORAGE, ADAPTIVE>(A, fma3(ds, w3, C), w4, n4, unused);
-                const float3 k4 = (1.0f / n4) * gp4;
+                const float3 k4 = __fdividef(1.0f, n4) * gp4;
                 const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
                 dnew = renormalize(wr, fma3(ds * (1.0f / 6.0f), ksum, d));
                 const float3 dpos = (1.0f / 6.0f) * (d + 2.0f * (d2 + d3) + d4);
@@ -312,17 +361,20 @@ __global__ void __launch_bounds__(128) march_kernel(const TraceArgs A) {
                 const float3 w = wr + d;
                 const float3 gp = perp_rate<STORAGE, ADAPTIVE>(A, C, w, n, gpn);
                 ds = step_length<ADAPTIVE>(A, n, gpn);
-                dnew = renormalize(wr, fma3(ds / n, gp, d));
+                dnew = renormalize(wr, fma3(__fdividef(ds, n), gp, d));
                 inc = ds * (wr + dnew);
             }
             float3 nhi, err;
-            two_sum(hi.x, inc.x, nhi.x, err.x);
-            two_sum(hi.y, inc.y, nhi.y, err.y);
-            two_sum(hi.z, inc.z, nhi.z, err.z);
+            fast_two_sum(hi.x, inc.x, nhi.x, err.x);
+            fast_two_sum(hi.y, inc.y, nhi.y, err.y);
+            fast_two_sum(hi.z, inc.z, nhi.z, err.z);
             const float3 nlo = lo + err;
-            if (outside(A, nhi + nlo)) {
-                const float tau = exit_fraction(A, hi, lo, inc);
-                ep = hi + fma3(tau, inc, lo);
+            const float3 P = make_float3((nhi.x - B) + nlo.x, (nhi.y - B) + nlo.y,
+                                         (nhi.z - B) + nlo.z);
+            if (outside(A, P)) {
+                const float3 h0 = make_float3(hi.x - B, hi.y - B, hi.z - B);  // exact
+                const float tau = exit_fraction(A, h0, lo, inc);
+                ep = h0 + fma3(tau, inc, lo);
                 ed = wr + dnew;
                 flags |= HH_FLAG_EXITED;
                 ++k;
@@ -334,7 +386,7 @@ __global__ void __launch_bounds__(128) march_kernel(const TraceArgs A) {
         }
         if (!(flags & HH_FLAG_EXITED)) {
             flags |= HH_FLAG_MAXSTEPS;
-            ep = hi + lo;
+            ep = make_float3((hi.x - B) + lo.x, (hi.y - B) + lo.y, (hi.z - B) + lo.z);
             ed = wr + d;
         }
     }
@@ -368,12 +420,27 @@ void launch_one(const TraceArgs& A, cudaStream_t s) {
 
 cudaError_t launch_trace(const hh_volume_s* vol, const hh_camera& cam, const hh_step_params& P,
                          const hh_background& bg, const hh_view_out& out, cudaStream_t s) {
+    if (vol->layout != HH_LAYOUT_BRICK2) return cudaErrorInvalidValue;
     TraceArgs A;
     A.vol = vol->data;
     A.scales = vol->scales_dev;
     A.nx = vol->nx;
     A.ny = vol->ny;
     A.nz = vol->nz;
+    A.bx = vol->bx;
+    A.bxy = vol->bxy;
+    A.by8 = vol->bx * 8u;
+    A.bz8 = vol->bxy * 8u;
+    {
+        // bias: a power of two B with B >= 2 * step and B >= extent + step, so
+        // positions in [-step, extent + step] keep hi in [B/2, 2B]
+        const float step = P.adaptive ? P.h_max : P.h_fixed;
+        const float need = fmaxf(static_cast<float>(max(vol->nx, max(vol->ny, vol->nz))) + step,
+                                 2.0f * step);
+        float B = 8.0f;
+        while (B < need) B *= 2.0f;
+        A.bias = B;
+    }
     A.eye = make_float3(cam.eye[0], cam.eye[1], cam.eye[2]);
     A.look = make_float3(cam.look_at[0], cam.look_at[1], cam.look_at[2]);
     A.up = make_float3(cam.up[0], cam.up[1], cam.up[2]);

@@ -103,6 +103,7 @@ extern "C" hh_status hh_build_index_field_noalloc(const hh_particles* particles,
     out.ny = grid->ny;
     out.nz = grid->nz;
     out.storage = HH_STORE_FP32;
+    out.layout = HH_LAYOUT_LINEAR;  // the documented x-fastest output
     out.h_kernel = grid->h_kernel;
     out.data = vol4_dev;
     out.bytes = nvox * 16;

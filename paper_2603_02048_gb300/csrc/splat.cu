@@ -2,25 +2,35 @@
 // rho(x_v) = sum_p m_p W(|x_v - x_p|, h) at voxel centres, W the M4 cubic
 // spline with support 2h.
 //
-// One warp per particle. The lanes walk the particle's footprint (the voxels
-// whose centres lie within 2h on every axis: 8^3 for h = 2) x-fastest, so a
-// warp's 32 atomics cover four 8-float rows (four 32-byte sectors) and
-// compile to fire-and-forget reductions in L2.
+// One warp per particle. The lanes form an 8 (x) by 4 (y) grid that walks the
+// particle's footprint (the voxels whose centres lie within 2h on every axis:
+// 8^3 for h = 2) one z slice and four rows at a time, so a warp's atomics
+// cover four 8-float rows (four 32-byte sectors) and compile to
+// fire-and-forget reductions in L2. dz^2 and dy^2 are hoisted out of the
+// inner loop, indices are 32-bit (grids hold fewer than 2^31 voxels) and
+// voxels beyond the support (r^2 >= 4h^2, about half of the footprint box)
+// skip the square root and the atomic.
 #include "hh_internal.h"
 
 namespace hh {
 namespace {
 
 // M4 cubic spline, q = r / h: norm (1 - 3/2 q^2 + 3/4 q^3) on [0,1),
-// norm (2 - q)^3 / 4 on [1,2), 0 beyond; norm = 1 / (pi h^3).
+// norm (2 - q)^3 / 4 on [1,2), 0 beyond; norm = 1 / (pi h^3). Both pieces are
+// evaluated and selected, so lanes on either side of q = 1 do not diverge.
 __device__ __forceinline__ float m4_kernel(float r, float inv_h, float norm) {
-    float q = r * inv_h;
-    if (q < 1.0f) return norm * (1.0f - 1.5f * q * q + 0.75f * q * q * q);
-    if (q < 2.0f) {
-        float t = 2.0f - q;
-        return norm * 0.25f * t * t * t;
-    }
-    return 0.0f;
+    const float q = r * inv_h;
+    const float inner = fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
+    const float t = fmaxf(2.0f - q, 0.0f);
+    const float outer = 0.25f * t * t * t;
+    return norm * (q < 1.0f ? inner : outer);
+}
+
+// Hardware approximate square root (PTX sqrt.approx.f32, ~1 ulp).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 // First and last voxel index along one axis whose centre lies within `reach`
@@ -44,22 +54,31 @@ __global__ void __launch_bounds__(256) splat_warp_kernel(const float4* __restric
     footprint(q.x, 2.0f * h, nx, x0, x1);
     footprint(q.y, 2.0f * h, ny, y0, y1);
     footprint(q.z, 2.0f * h, nz, z0, z1);
-    const int ex = x1 - x0 + 1, ey = y1 - y0 + 1, ez = z1 - z0 + 1;
-    if (ex <= 0 || ey <= 0 || ez <= 0) return;
-    const int plane = ex * ey;
-    const int total = plane * ez;
-    for (int t = lane; t < total; t += 32) {
-        const int k = t / plane;
-        const int r = t - k * plane;
-        const int j = r / ex;
-        const int i = r - j * ex;
-        const int gi = x0 + i, gj = y0 + j, gk = z0 + k;
-        const float dx = (static_cast<float>(gi) + 0.5f) - q.x;
-        const float dy = (static_cast<float>(gj) + 0.5f) - q.y;
-        const float dz = (static_cast<float>(gk) + 0.5f) - q.z;
-        const float w = m4_kernel(sqrtf(dx * dx + dy * dy + dz * dz), inv_h, norm);
-        if (w > 0.0f)
-            atomicAdd(rho + (static_cast<size_t>(gk) * ny + gj) * nx + gi, q.w * w);
+    if (x1 < x0 || y1 < y0 || z1 < z0) return;
+    const int lx = lane & 7, ly = lane >> 3;
+    const float reach2 = 4.0f * h * h;
+    const float m = q.w;
+    for (int k = z0; k <= z1; ++k) {
+        const float dz = (static_cast<float>(k) + 0.5f) - q.z;
+        const float dz2 = dz * dz;
+        if (!(dz2 < reach2)) continue;  // warp-uniform: the slice is outside the support
+        const unsigned plane = static_cast<unsigned>(k) * static_cast<unsigned>(ny);
+        for (int jb = y0; jb <= y1; jb += 4) {
+            const int j = jb + ly;
+            const float dy = (static_cast<float>(j) + 0.5f) - q.y;
+            const float dyz2 = fmaf(dy, dy, dz2);
+            float* row = rho + (plane + static_cast<unsigned>(min(j, y1))) * static_cast<unsigned>(nx);
+            const bool row_ok = j <= y1 && dyz2 < reach2;
+            for (int ib = x0; ib <= x1; ib += 8) {
+                const int i = ib + lx;
+                const float dx = (static_cast<float>(i) + 0.5f) - q.x;
+                const float r2 = fmaf(dx, dx, dyz2);
+                if (row_ok && i <= x1 && r2 < reach2) {
+                    const float w = m4_kernel(sqrt_approx(r2), inv_h, norm);
+                    if (w > 0.0f) atomicAdd(row + i, m * w);
+                }
+            }
+        }
     }
 }
 
