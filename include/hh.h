@@ -218,6 +218,62 @@ hh_status hh_trace(hh_volume vol, const hh_camera* cams, int n_cams,
                    const hh_view_out* outs, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Batched multi-view launches                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Many views of one volume in one persistent launch: the per-ray work is
+ * hh_trace's (results are bit-identical to it), but every warp pulls
+ * 32-pixel tiles of any view from one atomic counter, so views of uneven
+ * size share the GPU without per-view tails. Multi-camera rendering of one
+ * shared volume is the paper's scaling axis (Sec. 4.1, Table 1) and its
+ * central claim (Sec. 4.2, multi-view consistency). */
+typedef struct hh_batch_s* hh_batch;
+
+/* Launch shape of a batch (hh_batch_autotune searches it). */
+typedef struct {
+    int block_threads; /* threads per block, a multiple of 32 in [32, 256]      */
+    int blocks_per_sm; /* resident blocks per SM; 0 = the occupancy maximum     */
+    int refill_min;    /* warp-level compaction: idle lanes take new pixels once
+                          at least this many lanes of the warp are idle (1..32;
+                          32 = only when the whole warp is idle)              */
+    int tile_w;        /* pixel tile of a warp: tile_w x (32 / tile_w), 4/8/16 */
+} hh_batch_config;
+
+/* Creates a batch of n_cams views (1..4096) over `vol`; outs[i] belongs to
+ * cams[i] (same layout and rules as hh_trace). The library copies the view
+ * table to the device (cudaMalloc + synchronous copy); the volume, the
+ * background and the output buffers stay owned by the caller and must
+ * outlive the batch. Default configuration: {128, 0, 32, 8}. */
+hh_status hh_batch_create(hh_volume vol, const hh_camera* cams, int n_cams,
+                          const hh_step_params* params, const hh_background* bg,
+                          const hh_view_out* outs, hh_batch* out);
+
+/* Sets / reads the launch shape. Setting a new tile_w re-uploads the view
+ * table (synchronous). Get reports blocks_per_sm resolved to a number. */
+hh_status hh_batch_set_config(hh_batch b, const hh_batch_config* cfg);
+hh_status hh_batch_get_config(hh_batch b, hh_batch_config* cfg);
+
+/* Times candidate configurations (tile 8x4 / 4x8 / 16x2; 64, 128, 256 threads;
+ * compaction at 32, 16, 8 idle lanes; full or half occupancy) with CUDA events
+ * on `stream`, each as the median of |reps| launches, and keeps the fastest.
+ * Results are cached in the process by workload (grid, storage, schedule,
+ * view resolutions); reps > 0 reuses a cached result, reps < 0 re-measures.
+ * Synchronous; writes the outputs like a launch. */
+hh_status hh_batch_autotune(hh_batch b, int reps, void* stream, hh_batch_config* best);
+
+/* Enqueues one persistent launch (a counter reset plus one kernel) on
+ * `stream`; it can be captured into a CUDA graph by the caller. */
+hh_status hh_batch_launch(hh_batch b, void* stream);
+
+/* Same launch through a CUDA graph the batch captures on its first call (on
+ * `stream`, which must be a created stream, not the legacy default) and
+ * replays afterwards. A new configuration or stream re-captures. */
+hh_status hh_batch_launch_graph(hh_batch b, void* stream);
+
+/* Releases the batch (its graph, view table and counter). NULL is ok. */
+hh_status hh_batch_free(hh_batch b);
+
+/* ---------------------------------------------------------------------- */
 /* Diagnostics                                                             */
 /* ---------------------------------------------------------------------- */
 

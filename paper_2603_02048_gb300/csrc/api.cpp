@@ -127,6 +127,8 @@ hh_status volume_from(const float* rho_dev, const hh_grid* grid, float K, cudaSt
     return ok();
 }
 
+}  // namespace
+
 hh_status check_params(const hh_step_params* P) {
     if (!P) return fail(HH_ERR_INVALID_ARG, "step params is NULL");
     if (P->stepper != HH_STEP_EULER_PAPER && P->stepper != HH_STEP_RK4)
@@ -165,7 +167,6 @@ hh_status check_camera(const hh_camera& c, int i) {
     return HH_OK;
 }
 
-}  // namespace
 }  // namespace hh
 
 using namespace hh;

@@ -26,6 +26,12 @@
 // corner fetches per step share cache lines in L1. The volume is stored in
 // 2x2x2 micro-bricks (BRICK2), which spreads the distinct voxels of a warp's
 // corner load over all L1 bank groups.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
 #include "hh_internal.h"
 
 namespace hh {
@@ -33,25 +39,33 @@ namespace {
 
 constexpr float kPi = 3.14159265358979323846f;
 
-struct TraceArgs {
+// Volume-side arguments of a launch (shared by every view).
+struct VolArgs {
     const void* vol;
     const float* scales;
     int nx, ny, nz;
     unsigned bx, bxy;   // BRICK2 bricks along x and per xy plane
     unsigned by8, bz8;  // BRICK2 strides (in elements) of one brick step in y and z
     float bias;         // power of two above every coordinate and step
-    float3 eye, look, up;
-    float vfov_deg;
-    int W, H;
     float h_fixed, h_min, h_max, theta, eps;
     int max_steps;
     const uint8_t* bg;
     int bgW, bgH;
+};
+
+// View-side arguments: the camera, the caller's output buffers and the
+// view's place in a batch's tile list.
+struct ViewArgs {
+    float3 eye, look, up;
+    float vfov_deg;
+    int W, H;
     float* rgb;
     float* exit_pos;
     float* exit_dir;
     int32_t* steps;
     uint32_t* flags;
+    int tiles_x;     // 8x4-pixel tiles per row
+    int tile_begin;  // index of the view's first tile in the batch
 };
 
 struct Sample {
@@ -120,7 +134,7 @@ __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
 // trilinear interpolation); FP16 volumes are interpolated as stored and
 // scaled once afterwards.
 template <int STORAGE>
-__device__ __forceinline__ Sample fetch(const TraceArgs& A, float3 p) {
+__device__ __forceinline__ Sample fetch(const VolArgs& A, float3 p) {
     int ix, iy, iz;
     float fx, fy, fz;
     axis_cell(p.x, A.nx, ix, fx);
@@ -198,7 +212,7 @@ __device__ __forceinline__ Sample fetch(const TraceArgs& A, float3 p) {
 
 // Eq. 18 (second form) or the fixed step.
 template <bool ADAPTIVE>
-__device__ __forceinline__ float step_length(const TraceArgs& A, float n, float gperp_norm) {
+__device__ __forceinline__ float step_length(const VolArgs& A, float n, float gperp_norm) {
     if (!ADAPTIVE) return A.h_fixed;
     return fminf(fmaxf(__fdividef(n * A.theta, gperp_norm + A.eps), A.h_min), A.h_max);
 }
@@ -214,7 +228,7 @@ __device__ __forceinline__ float3 renormalize(float3 wr, float3 d1) {
 
 // Colour of direction d in the equirect background (bilinear, u wraps,
 // v clamps; value / 255).
-__device__ __forceinline__ float3 background(const TraceArgs& A, float3 d) {
+__device__ __forceinline__ float3 background(const VolArgs& A, float3 d) {
     const float phi = atan2f(d.y, d.x);
     const float theta = atan2f(sqrtf(d.x * d.x + d.y * d.y), d.z);
     const float W = static_cast<float>(A.bgW), H = static_cast<float>(A.bgH);
@@ -241,7 +255,7 @@ __device__ __forceinline__ float3 background(const TraceArgs& A, float3 d) {
 }
 
 // Ray through the centre of pixel (px, py); row 0 at the top.
-__device__ __forceinline__ float3 primary_ray(const TraceArgs& A, int px, int py) {
+__device__ __forceinline__ float3 primary_ray(const ViewArgs& A, int px, int py) {
     const float3 f = normalized(A.look - A.eye);
     const float3 r = normalized(cross(f, A.up));
     const float3 u = cross(r, f);
@@ -254,7 +268,7 @@ __device__ __forceinline__ float3 primary_ray(const TraceArgs& A, int px, int py
 
 // Slab test of o + t d against [0,nx]x[0,ny]x[0,nz]; hit iff
 // t_out >= max(t_in, 0). An axis with d = 0 misses when o is outside it.
-__device__ __forceinline__ bool slab(const TraceArgs& A, float3 o, float3 d, float& t_in) {
+__device__ __forceinline__ bool slab(const VolArgs& A, float3 o, float3 d, float& t_in) {
     float tin = -INFINITY, tout = INFINITY;
     const float oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
     const float bx[3] = {static_cast<float>(A.nx), static_cast<float>(A.ny),
@@ -274,14 +288,14 @@ __device__ __forceinline__ bool slab(const TraceArgs& A, float3 o, float3 d, flo
     return tout >= fmaxf(tin, 0.0f);
 }
 
-__device__ __forceinline__ bool outside(const TraceArgs& A, float3 p) {
+__device__ __forceinline__ bool outside(const VolArgs& A, float3 p) {
     return p.x < 0.0f || p.y < 0.0f || p.z < 0.0f || p.x > static_cast<float>(A.nx) ||
            p.y > static_cast<float>(A.ny) || p.z > static_cast<float>(A.nz);
 }
 
 // Fraction tau in [0, 1] of the increment `inc` from (hi + lo) at which the
 // segment leaves the box (the slab exit along the segment).
-__device__ __forceinline__ float exit_fraction(const TraceArgs& A, float3 hi, float3 lo,
+__device__ __forceinline__ float exit_fraction(const VolArgs& A, float3 hi, float3 lo,
                                                float3 inc) {
     const float h3[3] = {hi.x, hi.y, hi.z}, l3[3] = {lo.x, lo.y, lo.z};
     const float i3[3] = {inc.x, inc.y, inc.z};
@@ -297,7 +311,7 @@ __device__ __forceinline__ float exit_fraction(const TraceArgs& A, float3 hi, fl
 }
 
 template <int STORAGE, bool ADAPTIVE>
-__device__ __forceinline__ float3 perp_rate(const TraceArgs& A, float3 p, float3 w, float& n,
+__device__ __forceinline__ float3 perp_rate(const VolArgs& A, float3 p, float3 w, float& n,
                                             float& gperp_norm) {
     const Sample s = fetch<STORAGE>(A, p);
     n = 1.0f + s.dn;
@@ -307,121 +321,282 @@ __device__ __forceinline__ float3 perp_rate(const TraceArgs& A, float3 p, float3
     return gp;
 }
 
+// Per-ray state of the march: primary direction w_ref, deflection d, biased
+// compensated position (hi, lo), steps taken and flags.
+struct RayState {
+    float3 wr, hi, lo, d;
+    int k;
+    uint32_t flags;
+};
+
+// Ray generation and slab entry (flags = HIT when the ray enters the box).
+__device__ __forceinline__ void ray_begin(const VolArgs& V, const ViewArgs& C, int px, int py,
+                                          RayState& R) {
+    R.wr = primary_ray(C, px, py);
+    R.k = 0;
+    R.flags = 0;
+    R.d = make_float3(0.0f, 0.0f, 0.0f);
+    R.hi = R.lo = R.d;
+    float t_in;
+    if (slab(V, C.eye, R.wr, t_in)) {
+        R.flags = HH_FLAG_HIT;
+        // position = (hi - B) + lo with hi = position + B (see the header)
+        const float3 entry = fma3(fmaxf(t_in, 0.0f), R.wr, C.eye);
+        fast_two_sum(V.bias, entry.x, R.hi.x, R.lo.x);
+        fast_two_sum(V.bias, entry.y, R.hi.y, R.lo.y);
+        fast_two_sum(V.bias, entry.z, R.hi.z, R.lo.z);
+    }
+}
+
+__device__ __forceinline__ float3 ray_position(const VolArgs& V, const RayState& R) {
+    const float B = V.bias;
+    return make_float3((R.hi.x - B) + R.lo.x, (R.hi.y - B) + R.lo.y, (R.hi.z - B) + R.lo.z);
+}
+
+// One step of Eq. 16 (or RK4) with the Eq. 18 (or fixed) step length.
+// Returns true when the step leaves the box: then ep / ed hold the exit
+// point on the face and the new direction.
 template <int STORAGE, int STEPPER, bool ADAPTIVE>
-__global__ void __launch_bounds__(128, (STEPPER == HH_STEP_RK4) ? 6 : 8) march_kernel(const TraceArgs A) {
+__device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& ep, float3& ed) {
+    const float B = V.bias;
+    const float3 wr = R.wr, d = R.d;
+    const float3 C = ray_position(V, R);
+    float ds;
+    float3 dnew, inc;
+    if (STEPPER == HH_STEP_RK4) {
+        float n1, gpn, n2, n3, n4, unused;
+        const float3 w1 = wr + d;
+        const float3 gp1 = perp_rate<STORAGE, ADAPTIVE>(V, C, w1, n1, gpn);
+        ds = step_length<ADAPTIVE>(V, n1, gpn);
+        const float hds = 0.5f * ds;
+        const float3 k1 = __fdividef(1.0f, n1) * gp1;
+        const float3 d2 = fma3(hds, k1, d);
+        const float3 w2 = wr + d2;
+        const float3 gp2 = perp_rate<STORAGE, ADAPTIVE>(V, fma3(hds, w1, C), w2, n2, unused);
+        const float3 k2 = __fdividef(1.0f, n2) * gp2;
+        const float3 d3 = fma3(hds, k2, d);
+        const float3 w3 = wr + d3;
+        const float3 gp3 = perp_rate<STORAGE, ADAPTIVE>(V, fma3(hds, w2, C), w3, n3, unused);
+        const float3 k3 = __fdividef(1.0f, n3) * gp3;
+        const float3 d4 = fma3(ds, k3, d);
+        const float3 w4 = wr + d4;
+        const float3 gp4 = perp_rate<STORAGE, ADAPTIVE>(V, fma3(ds, w3, C), w4, n4, unused);
+        const float3 k4 = __fdividef(1.0f, n4) * gp4;
+        const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
+        dnew = renormalize(wr, fma3(ds * (1.0f / 6.0f), ksum, d));
+        const float3 dpos = (1.0f / 6.0f) * (d + 2.0f * (d2 + d3) + d4);
+        inc = ds * (wr + dpos);
+    } else {
+        float n, gpn;
+        const float3 w = wr + d;
+        const float3 gp = perp_rate<STORAGE, ADAPTIVE>(V, C, w, n, gpn);
+        ds = step_length<ADAPTIVE>(V, n, gpn);
+        dnew = renormalize(wr, fma3(__fdividef(ds, n), gp, d));
+        inc = ds * (wr + dnew);
+    }
+    float3 nhi, err;
+    fast_two_sum(R.hi.x, inc.x, nhi.x, err.x);
+    fast_two_sum(R.hi.y, inc.y, nhi.y, err.y);
+    fast_two_sum(R.hi.z, inc.z, nhi.z, err.z);
+    const float3 nlo = R.lo + err;
+    const float3 P = make_float3((nhi.x - B) + nlo.x, (nhi.y - B) + nlo.y, (nhi.z - B) + nlo.z);
+    ++R.k;
+    if (outside(V, P)) {
+        const float3 h0 = make_float3(R.hi.x - B, R.hi.y - B, R.hi.z - B);  // exact
+        const float tau = exit_fraction(V, h0, R.lo, inc);
+        ep = h0 + fma3(tau, inc, R.lo);
+        ed = wr + dnew;
+        R.flags |= HH_FLAG_EXITED;
+        return true;
+    }
+    R.hi = nhi;
+    R.lo = nlo;
+    R.d = dnew;
+    return false;
+}
+
+// Final state, background lookup and the writes of one pixel. A ray that
+// missed reports the eye and its primary direction; one that ran out of
+// steps reports its current state (MAXSTEPS).
+__device__ __forceinline__ void ray_end(const VolArgs& V, const ViewArgs& C, int px, int py,
+                                        const RayState& R, float3 ep, float3 ed) {
+    uint32_t flags = R.flags;
+    if (!(flags & HH_FLAG_HIT)) {
+        ep = C.eye;
+        ed = R.wr;
+    } else if (!(flags & HH_FLAG_EXITED)) {
+        flags |= HH_FLAG_MAXSTEPS;
+        ep = ray_position(V, R);
+        ed = R.wr + R.d;
+    }
+    const float3 rgb = background(V, ed);
+    const size_t pix = static_cast<size_t>(py) * C.W + px;
+    C.rgb[3 * pix + 0] = rgb.x;
+    C.rgb[3 * pix + 1] = rgb.y;
+    C.rgb[3 * pix + 2] = rgb.z;
+    if (C.exit_pos) {
+        C.exit_pos[3 * pix + 0] = ep.x;
+        C.exit_pos[3 * pix + 1] = ep.y;
+        C.exit_pos[3 * pix + 2] = ep.z;
+    }
+    if (C.exit_dir) {
+        C.exit_dir[3 * pix + 0] = ed.x;
+        C.exit_dir[3 * pix + 1] = ed.y;
+        C.exit_dir[3 * pix + 2] = ed.z;
+    }
+    if (C.steps) C.steps[pix] = R.k;
+    if (C.flags) C.flags[pix] = flags;
+}
+
+// One view, one thread per pixel: a block of 128 threads covers 16x8 pixels,
+// each warp an 8x4 tile.
+template <int STORAGE, int STEPPER, bool ADAPTIVE>
+__global__ void __launch_bounds__(128, (STEPPER == HH_STEP_RK4) ? 6 : 8)
+    march_kernel(const VolArgs V, const ViewArgs C) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-    if (px >= A.W || py >= A.H) return;
+    if (px >= C.W || py >= C.H) return;
+    RayState R;
+    float3 ep = C.eye, ed = C.eye;
+    ray_begin(V, C, px, py, R);
+    if (R.flags & HH_FLAG_HIT)
+        while (R.k < V.max_steps && !ray_step<STORAGE, STEPPER, ADAPTIVE>(V, R, ep, ed)) {
+        }
+    ray_end(V, C, px, py, R, ep, ed);
+}
 
-    const float3 wr = primary_ray(A, px, py);
-    float3 ep = A.eye, ed = wr;
-    uint32_t flags = 0;
-    int k = 0;
-    float t_in;
-    if (slab(A, A.eye, wr, t_in)) {
-        flags = HH_FLAG_HIT;
-        // position = (hi - B) + lo with hi = position + B (see the header)
-        const float B = A.bias;
-        const float3 entry = fma3(fmaxf(t_in, 0.0f), wr, A.eye);
-        float3 hi, lo;
-        fast_two_sum(B, entry.x, hi.x, lo.x);
-        fast_two_sum(B, entry.y, hi.y, lo.y);
-        fast_two_sum(B, entry.z, hi.z, lo.z);
-        float3 d = make_float3(0.0f, 0.0f, 0.0f);
-        for (k = 0; k < A.max_steps; ++k) {
-            const float3 C = make_float3((hi.x - B) + lo.x, (hi.y - B) + lo.y, (hi.z - B) + lo.z);
-            float ds;
-            float3 dnew, inc;
-            if (STEPPER == HH_STEP_RK4) {
-                float n1, gpn, n2, n3, n4, unused;
-                const float3 w1 = wr + d;
-                const float3 gp1 = perp_rate<STORAGE, ADAPTIVE>(A, C, w1, n1, gpn);
-                ds = step_length<ADAPTIVE>(A, n1, gpn);
-                const float hds = 0.5f * ds;
-                const float3 k1 = __fdividef(1.0f, n1) * gp1;
-                const float3 d2 = fma3(hds, k1, d);
-                const float3 w2 = wr + d2;
-                const float3 gp2 = perp_rate<STORAGE, ADAPTIVE>(A, fma3(hds, w1, C), w2, n2, unused);
-                const float3 k2 = __fdividef(1.0f, n2) * gp2;
-                const float3 d3 = fma3(hds, k2, d);
-                const float3 w3 = wr + d3;
-                const float3 gp3 = perp_rate<STORAGE, ADAPTIVE>(A, fma3(hds, w2, C), w3, n3, unused);
-                const float3 k3 = __fdividef(1.0f, n3) * gp3;
-                const float3 d4 = fma3(ds, k3, d);
-                const float3 w4 = wr + d4;
-                const float3 gp4 = perp_rate<STORAGE, ADAPTIVE>(A, fma3(ds, w3, C), w4, n4, unused);
-                const float3 k4 = __fdividef(1.0f, n4) * gp4;
-                const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
-                dnew = renormalize(wr, fma3(ds * (1.0f / 6.0f), ksum, d));
-                const float3 dpos = (1.0f / 6.0f) * (d + 2.0f * (d2 + d3) + d4);
-                inc = ds * (wr + dpos);
-            } else {
-                float n, gpn;
-                const float3 w = wr + d;
-                const float3 gp = perp_rate<STORAGE, ADAPTIVE>(A, C, w, n, gpn);
-                ds = step_length<ADAPTIVE>(A, n, gpn);
-                dnew = renormalize(wr, fma3(__fdividef(ds, n), gp, d));
-                inc = ds * (wr + dnew);
+// Persistent batched march over many views of uneven size. Each warp pulls
+// 32-pixel tiles (tile_w x 32/tile_w pixels) of any view from one atomic
+// counter and marches them lane by lane. Warp-level compaction: when at
+// least refill_min lanes are idle (their rays left the volume, missed it or
+// ran out of steps), the idle lanes take the next pixels of the warp's
+// current tile (and of the next tile when it runs out) while the other lanes
+// keep marching; refill_min = 32 refills only when every lane is idle, i.e.
+// plain tile-at-a-time scheduling. The per-ray arithmetic is march_kernel's.
+template <int STORAGE, int STEPPER, bool ADAPTIVE>
+__global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : 4)
+    march_batch_kernel(const VolArgs V, const ViewArgs* __restrict__ views, int n_views,
+                       int total_tiles, int tile_w, unsigned* __restrict__ counter,
+                       int refill_min) {
+    extern __shared__ int s_begin[];  // first tile of each view, then total_tiles
+    for (int i = threadIdx.x; i <= n_views; i += blockDim.x)
+        s_begin[i] = i < n_views ? views[i].tile_begin : total_tiles;
+    __syncthreads();
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int tile_w_log2 = tile_w == 16 ? 4 : (tile_w == 8 ? 3 : 2);
+    int tile = 0, tile_view = 0, pos = 32;  // the warp's pixel stream (warp-uniform)
+    bool done = false, have = false;
+    int vi = 0, px = 0, py = 0;
+    RayState R;
+    float3 ep = make_float3(0.0f, 0.0f, 0.0f), ed = ep;
+    for (;;) {
+        const unsigned free_mask = __ballot_sync(FULL, !have);
+        if (!done && __popc(free_mask) >= refill_min) {
+            unsigned todo = free_mask;
+            while (todo && !done) {
+                if (pos >= 32) {
+                    int t = 0;
+                    if (lane == 0) t = static_cast<int>(atomicAdd(counter, 1u));
+                    t = __shfl_sync(FULL, t, 0);
+                    if (t >= total_tiles) {
+                        done = true;
+                        break;
+                    }
+                    int lo = 0, hi = n_views - 1;  // last view whose first tile <= t
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_begin[mid] <= t) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    tile = t;
+                    tile_view = lo;
+                    pos = 0;
+                }
+                const int avail = 32 - pos;
+                const int rank = __popc(todo & lt_mask);
+                const bool mine = ((todo >> lane) & 1u) && rank < avail;
+                if (mine) {
+                    const ViewArgs& C = views[tile_view];
+                    const int local = tile - s_begin[tile_view];
+                    const int p = pos + rank;
+                    const int ty = local / C.tiles_x, tx = local - ty * C.tiles_x;
+                    px = (tx << tile_w_log2) + (p & (tile_w - 1));
+                    py = ty * (32 >> tile_w_log2) + (p >> tile_w_log2);
+                    vi = tile_view;
+                    if (px < C.W && py < C.H) {
+                        ray_begin(V, C, px, py, R);
+                        if ((R.flags & HH_FLAG_HIT) && V.max_steps > 0) have = true;
+                        else ray_end(V, C, px, py, R, ep, ed);
+                    }
+                }
+                pos += min(avail, __popc(todo));
+                todo &= ~__ballot_sync(FULL, mine);
             }
-            float3 nhi, err;
-            fast_two_sum(hi.x, inc.x, nhi.x, err.x);
-            fast_two_sum(hi.y, inc.y, nhi.y, err.y);
-            fast_two_sum(hi.z, inc.z, nhi.z, err.z);
-            const float3 nlo = lo + err;
-            const float3 P = make_float3((nhi.x - B) + nlo.x, (nhi.y - B) + nlo.y,
-                                         (nhi.z - B) + nlo.z);
-            if (outside(A, P)) {
-                const float3 h0 = make_float3(hi.x - B, hi.y - B, hi.z - B);  // exact
-                const float tau = exit_fraction(A, h0, lo, inc);
-                ep = h0 + fma3(tau, inc, lo);
-                ed = wr + dnew;
-                flags |= HH_FLAG_EXITED;
-                ++k;
-                break;
+        }
+        if (__ballot_sync(FULL, have) == 0u) {
+            if (done) break;
+            continue;
+        }
+        if (have) {
+            if (ray_step<STORAGE, STEPPER, ADAPTIVE>(V, R, ep, ed) || R.k >= V.max_steps) {
+                ray_end(V, views[vi], px, py, R, ep, ed);
+                have = false;
             }
-            hi = nhi;
-            lo = nlo;
-            d = dnew;
-        }
-        if (!(flags & HH_FLAG_EXITED)) {
-            flags |= HH_FLAG_MAXSTEPS;
-            ep = make_float3((hi.x - B) + lo.x, (hi.y - B) + lo.y, (hi.z - B) + lo.z);
-            ed = wr + d;
         }
     }
-    const float3 rgb = background(A, ed);
-    const size_t pix = static_cast<size_t>(py) * A.W + px;
-    A.rgb[3 * pix + 0] = rgb.x;
-    A.rgb[3 * pix + 1] = rgb.y;
-    A.rgb[3 * pix + 2] = rgb.z;
-    if (A.exit_pos) {
-        A.exit_pos[3 * pix + 0] = ep.x;
-        A.exit_pos[3 * pix + 1] = ep.y;
-        A.exit_pos[3 * pix + 2] = ep.z;
-    }
-    if (A.exit_dir) {
-        A.exit_dir[3 * pix + 0] = ed.x;
-        A.exit_dir[3 * pix + 1] = ed.y;
-        A.exit_dir[3 * pix + 2] = ed.z;
-    }
-    if (A.steps) A.steps[pix] = k;
-    if (A.flags) A.flags[pix] = flags;
 }
 
 template <int STORAGE, int STEPPER, bool ADAPTIVE>
-void launch_one(const TraceArgs& A, cudaStream_t s) {
+void launch_one(const VolArgs& V, const ViewArgs& C, cudaStream_t s) {
     const dim3 block(128);
-    const dim3 grid((A.W + 15) / 16, (A.H + 7) / 8);
-    march_kernel<STORAGE, STEPPER, ADAPTIVE><<<grid, block, 0, s>>>(A);
+    const dim3 grid((C.W + 15) / 16, (C.H + 7) / 8);
+    march_kernel<STORAGE, STEPPER, ADAPTIVE><<<grid, block, 0, s>>>(V, C);
 }
 
-}  // namespace
+// Calls F<STORAGE, STEPPER, ADAPTIVE>::run(args...) for the runtime choice.
+template <template <int, int, bool> class F, typename... Args>
+void dispatch(int storage, int stepper, int adaptive, Args&&... args) {
+    const bool fp16 = storage == HH_STORE_FP16_SCALED, rk4 = stepper == HH_STEP_RK4;
+    if (!fp16 && !rk4 && !adaptive) F<HH_STORE_FP32, HH_STEP_EULER_PAPER, false>::run(args...);
+    if (!fp16 && !rk4 && adaptive) F<HH_STORE_FP32, HH_STEP_EULER_PAPER, true>::run(args...);
+    if (!fp16 && rk4 && !adaptive) F<HH_STORE_FP32, HH_STEP_RK4, false>::run(args...);
+    if (!fp16 && rk4 && adaptive) F<HH_STORE_FP32, HH_STEP_RK4, true>::run(args...);
+    if (fp16 && !rk4 && !adaptive) F<HH_STORE_FP16_SCALED, HH_STEP_EULER_PAPER, false>::run(args...);
+    if (fp16 && !rk4 && adaptive) F<HH_STORE_FP16_SCALED, HH_STEP_EULER_PAPER, true>::run(args...);
+    if (fp16 && rk4 && !adaptive) F<HH_STORE_FP16_SCALED, HH_STEP_RK4, false>::run(args...);
+    if (fp16 && rk4 && adaptive) F<HH_STORE_FP16_SCALED, HH_STEP_RK4, true>::run(args...);
+}
 
-cudaError_t launch_trace(const hh_volume_s* vol, const hh_camera& cam, const hh_step_params& P,
-                         const hh_background& bg, const hh_view_out& out, cudaStream_t s) {
-    if (vol->layout != HH_LAYOUT_BRICK2) return cudaErrorInvalidValue;
-    TraceArgs A;
+template <int ST, int SP, bool AD>
+struct SingleLaunch {
+    static void run(const VolArgs& V, const ViewArgs& C, cudaStream_t s) {
+        launch_one<ST, SP, AD>(V, C, s);
+    }
+};
+
+template <int ST, int SP, bool AD>
+struct BatchLaunch {
+    static void run(const VolArgs& V, const ViewArgs* views, int n_views, int total_tiles,
+                    int tile_w, unsigned* counter, int refill_min, int blocks, int threads,
+                    cudaStream_t s) {
+        march_batch_kernel<ST, SP, AD><<<blocks, threads, (n_views + 1) * sizeof(int), s>>>(
+            V, views, n_views, total_tiles, tile_w, counter, refill_min);
+    }
+};
+
+template <int ST, int SP, bool AD>
+struct BatchOccupancy {
+    static void run(int threads, size_t smem, int* blocks_per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, march_batch_kernel<ST, SP, AD>,
+                                                      threads, smem);
+    }
+};
+
+VolArgs make_vol_args(const hh_volume_s* vol, const hh_step_params& P, const hh_background& bg) {
+    VolArgs A;
     A.vol = vol->data;
     A.scales = vol->scales_dev;
     A.nx = vol->nx;
@@ -431,22 +606,14 @@ cudaError_t launch_trace(const hh_volume_s* vol, const hh_camera& cam, const hh_
     A.bxy = vol->bxy;
     A.by8 = vol->bx * 8u;
     A.bz8 = vol->bxy * 8u;
-    {
-        // bias: a power of two B with B >= 2 * step and B >= extent + step, so
-        // positions in [-step, extent + step] keep hi in [B/2, 2B]
-        const float step = P.adaptive ? P.h_max : P.h_fixed;
-        const float need = fmaxf(static_cast<float>(max(vol->nx, max(vol->ny, vol->nz))) + step,
-                                 2.0f * step);
-        float B = 8.0f;
-        while (B < need) B *= 2.0f;
-        A.bias = B;
-    }
-    A.eye = make_float3(cam.eye[0], cam.eye[1], cam.eye[2]);
-    A.look = make_float3(cam.look_at[0], cam.look_at[1], cam.look_at[2]);
-    A.up = make_float3(cam.up[0], cam.up[1], cam.up[2]);
-    A.vfov_deg = cam.vfov_deg;
-    A.W = cam.width;
-    A.H = cam.height;
+    // bias: a power of two B with B >= 2 * step and B >= extent + step, so
+    // positions in [-step, extent + step] keep hi in [B/2, 2B]
+    const float step = P.adaptive ? P.h_max : P.h_fixed;
+    const float need =
+        fmaxf(static_cast<float>(max(vol->nx, max(vol->ny, vol->nz))) + step, 2.0f * step);
+    float B = 8.0f;
+    while (B < need) B *= 2.0f;
+    A.bias = B;
     A.h_fixed = P.h_fixed;
     A.h_min = P.h_min;
     A.h_max = P.h_max;
@@ -456,24 +623,315 @@ cudaError_t launch_trace(const hh_volume_s* vol, const hh_camera& cam, const hh_
     A.bg = bg.rgb8_dev;
     A.bgW = bg.width;
     A.bgH = bg.height;
-    A.rgb = out.rgb;
-    A.exit_pos = out.exit_pos;
-    A.exit_dir = out.exit_dir;
-    A.steps = out.steps;
-    A.flags = out.flags;
-    const bool fp16 = vol->storage == HH_STORE_FP16_SCALED;
-    const bool rk4 = P.stepper == HH_STEP_RK4;
-    const bool adaptive = P.adaptive != 0;
-    if (!fp16 && !rk4 && !adaptive) launch_one<HH_STORE_FP32, HH_STEP_EULER_PAPER, false>(A, s);
-    if (!fp16 && !rk4 && adaptive) launch_one<HH_STORE_FP32, HH_STEP_EULER_PAPER, true>(A, s);
-    if (!fp16 && rk4 && !adaptive) launch_one<HH_STORE_FP32, HH_STEP_RK4, false>(A, s);
-    if (!fp16 && rk4 && adaptive) launch_one<HH_STORE_FP32, HH_STEP_RK4, true>(A, s);
-    if (fp16 && !rk4 && !adaptive) launch_one<HH_STORE_FP16_SCALED, HH_STEP_EULER_PAPER, false>(A, s);
-    if (fp16 && !rk4 && adaptive) launch_one<HH_STORE_FP16_SCALED, HH_STEP_EULER_PAPER, true>(A, s);
-    if (fp16 && rk4 && !adaptive) launch_one<HH_STORE_FP16_SCALED, HH_STEP_RK4, false>(A, s);
-    if (fp16 && rk4 && adaptive) launch_one<HH_STORE_FP16_SCALED, HH_STEP_RK4, true>(A, s);
+    return A;
+}
+
+ViewArgs make_view_args(const hh_camera& cam, const hh_view_out& out, int tile_w) {
+    ViewArgs C;
+    C.eye = make_float3(cam.eye[0], cam.eye[1], cam.eye[2]);
+    C.look = make_float3(cam.look_at[0], cam.look_at[1], cam.look_at[2]);
+    C.up = make_float3(cam.up[0], cam.up[1], cam.up[2]);
+    C.vfov_deg = cam.vfov_deg;
+    C.W = cam.width;
+    C.H = cam.height;
+    C.rgb = out.rgb;
+    C.exit_pos = out.exit_pos;
+    C.exit_dir = out.exit_dir;
+    C.steps = out.steps;
+    C.flags = out.flags;
+    C.tiles_x = (cam.width + tile_w - 1) / tile_w;
+    C.tile_begin = 0;
+    return C;
+}
+}  // namespace
+
+cudaError_t launch_trace(const hh_volume_s* vol, const hh_camera& cam, const hh_step_params& P,
+                         const hh_background& bg, const hh_view_out& out, cudaStream_t s) {
+    if (vol->layout != HH_LAYOUT_BRICK2) return cudaErrorInvalidValue;
+    const VolArgs V = make_vol_args(vol, P, bg);
+    const ViewArgs C = make_view_args(cam, out, 8);
+    dispatch<SingleLaunch>(vol->storage, P.stepper, P.adaptive, V, C, s);
     count_launch();
     return cudaGetLastError();
 }
 
 }  // namespace hh
+
+// ------------------------------------------------------------------------
+// Batched multi-view launches (hh_batch_*)
+// ------------------------------------------------------------------------
+struct hh_batch_s {
+    hh_volume vol = nullptr;
+    hh_step_params params{};
+    hh_background bg{};
+    std::vector<hh_camera> cams;
+    std::vector<hh_view_out> outs;
+    hh_batch_config cfg{};
+    int total_tiles = 0;
+    hh::ViewArgs* views_dev = nullptr;
+    unsigned* counter_dev = nullptr;
+    int sm_count = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+};
+
+namespace {
+
+using hh::fail;
+using hh::cuda_fail;
+
+void drop_graph(hh_batch b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_stream = nullptr;
+}
+
+// Uploads the view table for the current tile width (synchronous).
+hh_status upload_views(hh_batch b) {
+    std::vector<hh::ViewArgs> v(b->cams.size());
+    int tiles = 0;
+    const int tile_w = b->cfg.tile_w, tile_h = 32 / tile_w;
+    for (size_t i = 0; i < v.size(); ++i) {
+        v[i] = hh::make_view_args(b->cams[i], b->outs[i], tile_w);
+        v[i].tile_begin = tiles;
+        const int64_t t = static_cast<int64_t>(v[i].tiles_x) * ((b->cams[i].height + tile_h - 1) / tile_h);
+        if (tiles + t > (int64_t(1) << 30)) return fail(HH_ERR_INVALID_ARG, "batch has too many pixels");
+        tiles += static_cast<int>(t);
+    }
+    b->total_tiles = tiles;
+    cudaError_t e = cudaMemcpy(b->views_dev, v.data(), v.size() * sizeof(hh::ViewArgs),
+                               cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading the view table");
+    return HH_OK;
+}
+
+hh_status check_config(const hh_batch_config* c) {
+    if (!c) return fail(HH_ERR_INVALID_ARG, "config is NULL");
+    if (c->block_threads < 32 || c->block_threads > 256 || c->block_threads % 32)
+        return fail(HH_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
+    if (c->blocks_per_sm < 0 || c->blocks_per_sm > 64)
+        return fail(HH_ERR_INVALID_ARG, "blocks_per_sm must be in [0, 64]");
+    if (c->refill_min < 1 || c->refill_min > 32)
+        return fail(HH_ERR_INVALID_ARG, "refill_min must be in [1, 32]");
+    if (c->tile_w != 4 && c->tile_w != 8 && c->tile_w != 16)
+        return fail(HH_ERR_INVALID_ARG, "tile_w must be 4, 8 or 16");
+    return HH_OK;
+}
+
+int resident_blocks(hh_batch b, int threads) {
+    int bps = 0;
+    const size_t smem = (b->cams.size() + 1) * sizeof(int);
+    hh::dispatch<hh::BatchOccupancy>(b->vol->storage, b->params.stepper, b->params.adaptive,
+                                     threads, smem, &bps);
+    return std::max(bps, 1);
+}
+
+int grid_blocks(hh_batch b) {
+    const int bps = b->cfg.blocks_per_sm > 0 ? b->cfg.blocks_per_sm
+                                              : resident_blocks(b, b->cfg.block_threads);
+    return b->sm_count * bps;
+}
+
+// Counter reset + one persistent launch of `blocks` blocks (no host queries,
+// so it can run inside a stream capture).
+cudaError_t enqueue(hh_batch b, int blocks, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b->counter_dev, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const int threads = b->cfg.block_threads;
+    const hh::VolArgs V = hh::make_vol_args(b->vol, b->params, b->bg);
+    hh::dispatch<hh::BatchLaunch>(b->vol->storage, b->params.stepper, b->params.adaptive, V,
+                                  b->views_dev, static_cast<int>(b->cams.size()), b->total_tiles,
+                                  b->cfg.tile_w, b->counter_dev, b->cfg.refill_min, blocks,
+                                  threads, s);
+    hh::count_launch();
+    return cudaGetLastError();
+}
+
+// Autotuner results by workload signature (grid, storage, schedule, views).
+std::mutex g_tune_mutex;
+std::map<std::string, hh_batch_config> g_tune_cache;
+
+std::string signature(hh_batch b) {
+    std::string k = std::to_string(b->vol->nx) + "x" + std::to_string(b->vol->ny) + "x" +
+                    std::to_string(b->vol->nz) + "/" + std::to_string(b->vol->storage) + "/" +
+                    std::to_string(b->params.stepper) + std::to_string(b->params.adaptive);
+    for (const auto& c : b->cams) k += "/" + std::to_string(c.width) + "x" + std::to_string(c.height);
+    return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+hh_status hh_batch_create(hh_volume vol, const hh_camera* cams, int n_cams,
+                          const hh_step_params* params, const hh_background* bg,
+                          const hh_view_out* outs, hh_batch* out) {
+    if (!out) return fail(HH_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!vol) return fail(HH_ERR_INVALID_ARG, "volume is NULL");
+    if (n_cams < 1 || n_cams > 4096 || !cams || !outs)
+        return fail(HH_ERR_INVALID_ARG, "a batch needs 1 to 4096 cameras and outputs");
+    hh_status st = hh::check_params(params);
+    if (st != HH_OK) return st;
+    if (!bg || !bg->rgb8_dev || bg->width < 1 || bg->height < 2)
+        return fail(HH_ERR_INVALID_ARG, "background needs a device pointer, width >= 1, height >= 2");
+    for (int i = 0; i < n_cams; ++i) {
+        if ((st = hh::check_camera(cams[i], i)) != HH_OK) return st;
+        if (!outs[i].rgb) return fail(HH_ERR_INVALID_ARG, "view %d: rgb output is NULL", i);
+    }
+    hh_batch b = new (std::nothrow) hh_batch_s();
+    if (!b) return fail(HH_ERR_OOM, "host allocation failed");
+    b->vol = vol;
+    b->params = *params;
+    b->bg = *bg;
+    b->cams.assign(cams, cams + n_cams);
+    b->outs.assign(outs, outs + n_cams);
+    b->cfg = hh_batch_config{128, 0, 32, 8};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->views_dev), n_cams * sizeof(hh::ViewArgs));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->counter_dev), sizeof(unsigned));
+    if (e != cudaSuccess) {
+        cudaFree(b->views_dev);
+        delete b;
+        return cuda_fail(e, "batch allocation");
+    }
+    if ((st = upload_views(b)) != HH_OK) {
+        hh_batch_free(b);
+        return st;
+    }
+    *out = b;
+    return hh::ok();
+}
+
+hh_status hh_batch_set_config(hh_batch b, const hh_batch_config* cfg) {
+    if (!b) return fail(HH_ERR_INVALID_ARG, "batch is NULL");
+    hh_status st = check_config(cfg);
+    if (st != HH_OK) return st;
+    const bool retile = cfg->tile_w != b->cfg.tile_w;
+    b->cfg = *cfg;
+    drop_graph(b);
+    if (retile && (st = upload_views(b)) != HH_OK) return st;
+    return hh::ok();
+}
+
+hh_status hh_batch_get_config(hh_batch b, hh_batch_config* cfg) {
+    if (!b || !cfg) return fail(HH_ERR_INVALID_ARG, "batch or config is NULL");
+    *cfg = b->cfg;
+    if (cfg->blocks_per_sm == 0) cfg->blocks_per_sm = resident_blocks(b, b->cfg.block_threads);
+    return hh::ok();
+}
+
+hh_status hh_batch_launch(hh_batch b, void* stream) {
+    if (!b) return fail(HH_ERR_INVALID_ARG, "batch is NULL");
+    cudaError_t e = enqueue(b, grid_blocks(b), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    return hh::ok();
+}
+
+hh_status hh_batch_launch_graph(hh_batch b, void* stream) {
+    if (!b) return fail(HH_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!s) return fail(HH_ERR_INVALID_ARG, "graph launches need a created (non-default) stream");
+    if (b->exec && b->graph_stream != s) drop_graph(b);
+    if (!b->exec) {
+        const int blocks = grid_blocks(b);
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+        cudaError_t le = enqueue(b, blocks, s);
+        e = cudaStreamEndCapture(s, &b->graph);
+        if (le != cudaSuccess) {
+            drop_graph(b);
+            return cuda_fail(le, "batch launch during capture");
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+        if (e != cudaSuccess) {
+            drop_graph(b);
+            return cuda_fail(e, "graph capture");
+        }
+        b->graph_stream = s;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    hh::count_launch();
+    return hh::ok();
+}
+
+hh_status hh_batch_autotune(hh_batch b, int reps, void* stream, hh_batch_config* best) {
+    if (!b) return fail(HH_ERR_INVALID_ARG, "batch is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const std::string key = signature(b);
+    if (reps > 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            hh_status st = hh_batch_set_config(b, &it->second);
+            if (st == HH_OK && best) *best = it->second;
+            return st;
+        }
+    }
+    if (reps == 0) return fail(HH_ERR_INVALID_ARG, "reps must be non-zero");
+    const int n = reps < 0 ? -reps : reps;
+    std::vector<hh_batch_config> cand;
+    for (int tw : {8, 4, 16})
+        for (int th : {128, 256, 64})
+            for (int rm : {32, 16, 8})
+                for (int bps : {0, -2}) cand.push_back(hh_batch_config{th, bps, rm, tw});
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    hh_batch_config best_cfg = b->cfg;
+    hh_status st = HH_OK;
+    for (auto c : cand) {
+        if (c.blocks_per_sm < 0) c.blocks_per_sm = std::max(1, resident_blocks(b, c.block_threads) / 2);
+        if ((st = hh_batch_set_config(b, &c)) != HH_OK) break;
+        std::vector<float> t;
+        const int blocks = grid_blocks(b);
+        cudaError_t e = enqueue(b, blocks, s);  // warm-up
+        for (int r = 0; r < n && e == cudaSuccess; ++r) {
+            cudaEventRecord(e0, s);
+            e = enqueue(b, blocks, s);
+            cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t.push_back(ms);
+        }
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "autotune trial");
+            break;
+        }
+        std::sort(t.begin(), t.end());
+        const float med = t[t.size() / 2];
+        if (med < best_ms) {
+            best_ms = med;
+            best_cfg = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HH_OK) return st;
+    if ((st = hh_batch_set_config(b, &best_cfg)) != HH_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = best_cfg;
+    }
+    if (best) *best = best_cfg;
+    return hh::ok();
+}
+
+hh_status hh_batch_free(hh_batch b) {
+    if (!b) return hh::ok();
+    drop_graph(b);
+    cudaFree(b->views_dev);
+    cudaFree(b->counter_dev);
+    delete b;
+    return hh::ok();
+}
+
+}  // extern "C"

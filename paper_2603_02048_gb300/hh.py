@@ -69,6 +69,11 @@ class hh_view_out(ctypes.Structure):
                 ("flags", ctypes.c_void_p)]
 
 
+class hh_batch_config(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("refill_min", ctypes.c_int), ("tile_w", ctypes.c_int)]
+
+
 # Every symbol include/hh.h declares, with (restype, argtypes).
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -93,6 +98,16 @@ SIGNATURES = {
     "hh_trace": (ctypes.c_int, [_P, ctypes.POINTER(hh_camera), ctypes.c_int,
                                 ctypes.POINTER(hh_step_params), ctypes.POINTER(hh_background),
                                 ctypes.POINTER(hh_view_out), _P]),
+    "hh_batch_create": (ctypes.c_int, [_P, ctypes.POINTER(hh_camera), ctypes.c_int,
+                                       ctypes.POINTER(hh_step_params),
+                                       ctypes.POINTER(hh_background), ctypes.POINTER(hh_view_out),
+                                       ctypes.POINTER(_P)]),
+    "hh_batch_set_config": (ctypes.c_int, [_P, ctypes.POINTER(hh_batch_config)]),
+    "hh_batch_get_config": (ctypes.c_int, [_P, ctypes.POINTER(hh_batch_config)]),
+    "hh_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(hh_batch_config)]),
+    "hh_batch_launch": (ctypes.c_int, [_P, _P]),
+    "hh_batch_launch_graph": (ctypes.c_int, [_P, _P]),
+    "hh_batch_free": (ctypes.c_int, [_P]),
     "hh_last_error": (ctypes.c_char_p, []),
     "hh_kernel_launch_count": (ctypes.c_uint64, []),
 }
@@ -262,6 +277,75 @@ def hh_trace(vol: Volume, cams, params, bg, outs, stream=None):
     B = hh_background(_ptr(bg), int(bg.shape[1]), int(bg.shape[0]))
     _check(load().hh_trace(vol.handle, c_cams, n, ctypes.byref(P), ctypes.byref(B), c_outs,
                            _stream(stream)))
+
+
+class Batch:
+    """Owns an hh_batch handle and keeps its views' buffers alive."""
+
+    def __init__(self, handle: ctypes.c_void_p, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(load().hh_batch_free(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle is not None and self.handle.value:
+                load().hh_batch_free(self.handle)
+        except Exception:
+            pass
+
+
+def _views(cams, outs):
+    n = len(cams)
+    c_cams = (hh_camera * max(n, 1))(*[c if isinstance(c, hh_camera) else make_camera(c)
+                                       for c in cams])
+    c_outs = (hh_view_out * max(n, 1))(*[
+        hh_view_out(_ptr(o["rgb"]), _ptr(o.get("exit_pos")), _ptr(o.get("exit_dir")),
+                    _ptr(o.get("steps")), _ptr(o.get("flags"))) for o in outs])
+    return n, c_cams, c_outs
+
+
+def hh_batch_create(vol: Volume, cams, params, bg, outs) -> Batch:
+    n, c_cams, c_outs = _views(cams, outs)
+    P = params if isinstance(params, hh_step_params) else make_params(params)
+    B = hh_background(_ptr(bg), int(bg.shape[1]), int(bg.shape[0]))
+    out = ctypes.c_void_p()
+    _check(load().hh_batch_create(vol.handle, c_cams, n, ctypes.byref(P), ctypes.byref(B),
+                                  c_outs, ctypes.byref(out)))
+    return Batch(out, (vol, bg, outs))
+
+
+def hh_batch_set_config(b: Batch, block_threads=128, blocks_per_sm=0, refill_min=32, tile_w=8):
+    c = hh_batch_config(int(block_threads), int(blocks_per_sm), int(refill_min), int(tile_w))
+    _check(load().hh_batch_set_config(b.handle, ctypes.byref(c)))
+
+
+def hh_batch_get_config(b: Batch) -> dict:
+    c = hh_batch_config()
+    _check(load().hh_batch_get_config(b.handle, ctypes.byref(c)))
+    return {f: getattr(c, f) for f, _ in hh_batch_config._fields_}
+
+
+def hh_batch_autotune(b: Batch, reps: int = 3, stream=None) -> dict:
+    c = hh_batch_config()
+    _check(load().hh_batch_autotune(b.handle, int(reps), _stream(stream), ctypes.byref(c)))
+    return {f: getattr(c, f) for f, _ in hh_batch_config._fields_}
+
+
+def hh_batch_launch(b: Batch, stream=None):
+    _check(load().hh_batch_launch(b.handle, _stream(stream)))
+
+
+def hh_batch_launch_graph(b: Batch, stream=None):
+    _check(load().hh_batch_launch_graph(b.handle, _stream(stream)))
+
+
+def hh_batch_free(b: Batch):
+    b.close()
 
 
 def hh_last_error() -> str:
