@@ -6,6 +6,12 @@ onto a 256^3 grid (Sec. 3.3.1), Gladstone-Dale + gradient into the FP32
 1920x1080 view (Eqs. 14-18) with the background lookup.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload frame|precision|batch]
+
+--workload precision / batch time the FP16 multi-view configurations (8 views
+of 1280x720 on the 256^3 scene; 32 uneven views on a 512^3 volume from
+2,097,152 particles) through the persistent batched launch, and add the same
+views' per-view and plain FP32 single-view march rates for comparison.
 
 Prints one JSON line. `value` is Mrays/s of whole steps (primary rays over
 the device time of splat + field + march, inputs resident in HBM, L2 flushed
@@ -33,16 +39,9 @@ sys.path.insert(0, ROOT)
 
 import hh_inputs as hi  # noqa: E402
 
-L = 256
-DIMS = (L, L, L)
-N_PARTICLES = 262144
-WIDTH, HEIGHT = 1920, 1080
-THETA = hi.THETA_CALIBRATED
-METRIC = "curved-ray Mrays/s (1080p, 256^3, splat+field+march per frame)"
-WORKLOAD = ("262,144-particle plume splatted (M4, h=2) onto 256^3, FP32 dn/grad-n volume "
-            "(K_GD=2.26e-4), one 1920x1080 view 1.5 grid widths away (60 deg vfov), "
-            "Eq. 16 march with Eq. 18 adaptive step h in [0.125, 2], theta_max=3e-5, eps=1e-6")
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
+METRIC = "curved-ray Mrays/s (1080p, 256^3, splat+field+march per frame)"
+K_GD32 = float(np.float32(hi.K_GD))
 
 
 def f32(x):
@@ -55,11 +54,44 @@ def f32(x):
     return x
 
 
-def scene():
-    parts = hi.plume_particles(N_PARTICLES, L)
-    cam = f32(hi.orbit_camera(DIMS, 0.0, 0.0, WIDTH, HEIGHT))
-    params = f32(hi.params_euler_adaptive(DIMS, theta_max=THETA))
-    return parts, cam, params, hi.checker_background()
+# The workloads. "frame" is the headline (the default); the others are the
+# FP16 multi-view precision configuration and the 32-view batching one.
+WORKLOADS = {
+    "frame": {
+        "L": 256, "particles": 262144, "storage": "fp32", "views": "single", "mode": "trace",
+        "metric": METRIC,
+        "text": ("262,144-particle plume splatted (M4, h=2) onto 256^3, FP32 dn/grad-n volume "
+                 "(K_GD=2.26e-4), one 1920x1080 view 1.5 grid widths away (60 deg vfov), "
+                 "Eq. 16 march with Eq. 18 adaptive step h in [0.125, 2], theta_max=3e-5, "
+                 "eps=1e-6")},
+    "precision": {
+        "L": 256, "particles": 262144, "storage": "fp16", "views": "arc8", "mode": "batch",
+        "metric": "curved-ray Mrays/s (8 x 1280x720 arc, 256^3 FP16, splat+field+march)",
+        "text": ("the 256^3 plume with dn/grad-n stored FP16 with per-volume scales, 8 views "
+                 "1280x720 evenly over a 90 deg arc, one persistent batched launch "
+                 "(autotuned, CUDA graph), Eq. 16 adaptive, theta_max=3e-5")},
+    "batch": {
+        "L": 512, "particles": 2097152, "storage": "fp16", "views": "mix32", "mode": "batch",
+        "metric": "curved-ray Mrays/s (32 uneven views, 512^3 FP16, splat+field+march)",
+        "text": ("2,097,152-particle plume -> 512^3 FP16 dn/grad-n volume, 32 views of uneven "
+                 "resolution (256^2 .. 1920x1080, seeded mix, eyes 1.5 grid widths away), one "
+                 "persistent batched launch (autotuned, CUDA graph), Eq. 16 adaptive, "
+                 "theta_max=3e-5")},
+}
+
+
+def scene(wl: dict):
+    L = wl["L"]
+    dims = (L, L, L)
+    parts = hi.plume_particles(wl["particles"], L)
+    if wl["views"] == "single":
+        cams = [hi.orbit_camera(dims, 0.0, 0.0, 1920, 1080)]
+    elif wl["views"] == "arc8":
+        cams = hi.arc_cameras(dims, n=8, width=1280, height=720)
+    else:
+        cams = hi.view_mix(dims, n=32)
+    params = f32(hi.params_euler_adaptive(dims, theta_max=hi.THETA_CALIBRATED))
+    return dims, parts, f32(cams), params, hi.checker_background()
 
 
 def measured_peaks():
@@ -159,6 +191,24 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 # our arm
 # --------------------------------------------------------------------------- #
+def traffic_for(workload: str):
+    """DRAM bytes per march launch from the committed ncu capture, or None
+    when the march source has changed since the counters were taken."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "march_traffic.json")
+    src = os.path.join(ROOT, "paper_2603_02048_gb300", "csrc", "march.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if rec.get("march_cu_sha256") != sha:
+        return None
+    w = rec.get("workloads", {}).get(workload)
+    return None if w is None else w.get("dram_bytes_per_launch")
+
+
 def run_ours(args):
     import torch
 
@@ -174,36 +224,56 @@ def run_ours(args):
     hb.build()  # no-op when fresh; makes sure every rank sees the library
     hh.load()
 
-    parts, cam, params, bg = scene()
+    wl = WORKLOADS[args.workload]
+    dims, parts, cams, params, bg = scene(wl)
     parts_t = torch.from_numpy(parts).to(dev)
     bg_t = torch.from_numpy(bg).to(dev)
-    grid = hh.make_grid(DIMS, 2.0, "fp32")
-    K = float(np.float32(hi.K_GD))
-    n_rays = WIDTH * HEIGHT
-    rgb = torch.empty(n_rays * 3, device=dev)
+    grid = hh.make_grid(dims, 2.0, wl["storage"])
+    n_rays = sum(c["width"] * c["height"] for c in cams)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()  # inputs are on the device before any other stream uses them
+    stream = torch.cuda.Stream(device=dev) if wl["mode"] == "batch" else \
+        torch.cuda.current_stream(dev)
+    vol = hh.hh_build_index_field(parts_t, grid, K_GD32, stream)
 
     # step statistics (deterministic input -> the same steps every frame)
-    vol = hh.hh_build_index_field(parts_t, grid, K)
-    steps_t = torch.empty(n_rays, dtype=torch.int32, device=dev)
-    flags_t = torch.empty(n_rays, dtype=torch.int32, device=dev)
-    hh.hh_trace(vol, [cam], params, bg_t, [{"rgb": rgb, "steps": steps_t, "flags": flags_t}])
+    stats = [{"rgb": torch.empty(c["width"] * c["height"] * 3, device=dev),
+              "steps": torch.empty(c["width"] * c["height"], dtype=torch.int32, device=dev),
+              "flags": torch.empty(c["width"] * c["height"], dtype=torch.int32, device=dev)}
+             for c in cams]
+    with torch.cuda.stream(stream):
+        hh.hh_trace(vol, cams, params, bg_t, stats, stream)
     torch.cuda.synchronize()
-    total_steps = int(steps_t.sum().item())
-    hits = int((flags_t & 1).sum().item())
+    total_steps = sum(int(o["steps"].sum().item()) for o in stats)
+    hits = sum(int((o["flags"] & 1).sum().item()) for o in stats)
+    outs = [{"rgb": o["rgb"]} for o in stats]
+    del stats
+
+    batch = None
+    tuned = None
+    if wl["mode"] == "batch":
+        batch = hh.hh_batch_create(vol, cams, params, bg_t, outs)
+        with torch.cuda.stream(stream):
+            tuned = hh.hh_batch_autotune(batch, reps=3, stream=stream)
+
+    def march():
+        if batch is not None:
+            hh.hh_batch_launch_graph(batch, stream)
+        else:
+            hh.hh_trace(vol, cams, params, bg_t, outs, stream)
 
     def step(src, ev=None):
-        hh.hh_volume_rebuild(vol, src, K)
+        hh.hh_volume_rebuild(vol, src, K_GD32, stream)
         if ev is not None:
             ev[0].record(stream)
-        hh.hh_trace(vol, [cam], params, bg_t, [{"rgb": rgb}])
+        march()
         if ev is not None:
             ev[1].record(stream)
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        step(parts_t)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(parts_t)
     torch.cuda.synchronize()
 
     ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -214,11 +284,12 @@ def run_ours(args):
     with ClockSampler(local) as clocks:
         barrier(dist)
         torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.zero_()
-            ev_step[k][0].record(stream)
-            step(parts_t, ev_march[k])
-            ev_step[k][1].record(stream)
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.zero_()
+                ev_step[k][0].record(stream)
+                step(parts_t, ev_march[k])
+                ev_step[k][1].record(stream)
         torch.cuda.synchronize()
         barrier(dist)
     launches = hh.hh_kernel_launch_count() - launches0
@@ -227,23 +298,56 @@ def run_ours(args):
     ms_step = max_over_ranks(dist, sum(step_ms) / len(step_ms), dev)
     ms_march = sum(march_ms) / len(march_ms)
 
-    # end to end through the C ABI: pinned host particles in, image out
+    # end to end through the C ABI: pinned host particles in, images out
     host_parts = torch.from_numpy(parts).pin_memory()
-    host_rgb = torch.empty(n_rays * 3, dtype=torch.float32).pin_memory()
+    host_rgb = [torch.empty(o["rgb"].numel(), dtype=torch.float32).pin_memory() for o in outs]
     dev_parts = torch.empty_like(parts_t)
     e2e_ms = []
-    for k in range(0 if args.no_e2e else args.warmup + args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        dev_parts.copy_(host_parts, non_blocking=True)
-        step(dev_parts)
-        host_rgb.copy_(rgb, non_blocking=True)
-        b.record(stream)
-        torch.cuda.synchronize()
-        if k >= args.warmup:
-            e2e_ms.append(a.elapsed_time(b))
+    with torch.cuda.stream(stream):
+        for k in range(0 if args.no_e2e else args.warmup + args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dev_parts.copy_(host_parts, non_blocking=True)
+            step(dev_parts)
+            for h, o in zip(host_rgb, outs):
+                h.copy_(o["rgb"], non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                e2e_ms.append(a.elapsed_time(b))
     ms_e2e = max_over_ranks(dist, sum(e2e_ms) / max(len(e2e_ms), 1), dev)
+
+    # comparisons for the multi-view workloads: the same views as per-view
+    # hh_trace launches on this volume, and the plain FP32 single-view march
+    # (hh_trace on an FP32 volume of the same scene), march time only
+    compare = {}
+    if wl["mode"] == "batch" and not args.no_compare:
+        def time_march(fn, reps=10):
+            for _ in range(3):
+                fn()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(reps)]
+            with torch.cuda.stream(stream):
+                for e0, e1 in evs:
+                    flush.zero_()
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+            torch.cuda.synchronize()
+            return sum(a.elapsed_time(b) for a, b in evs) / reps
+
+        with torch.cuda.stream(stream):
+            ms_pv = time_march(lambda: hh.hh_trace(vol, cams, params, bg_t, outs, stream))
+            v32 = hh.hh_build_index_field(parts_t, hh.make_grid(dims, 2.0, "fp32"), K_GD32,
+                                          stream)
+            ms_32 = time_march(lambda: hh.hh_trace(v32, cams, params, bg_t, outs, stream))
+            v32.close()
+        compare = {"batched_march_Mrays_s": round(n_rays / (ms_march * 1e-3) / 1e6, 3),
+                   "per_view_launches_march_Mrays_s": round(n_rays / (ms_pv * 1e-3) / 1e6, 3),
+                   "fp32_single_view_march_Mrays_s": round(n_rays / (ms_32 * 1e-3) / 1e6, 3)}
+    if batch is not None:
+        batch.close()
     vol.close()
 
     if rank != 0:
@@ -251,13 +355,18 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     peak, peak_kind = measured_peaks()
-    # algorithmic bytes of the march: 8 corners x 16 B per Eq. 16 step, plus
-    # per ray 12 B of RGB out and 4 x 3 B of background texels
-    march_bytes = total_steps * 128 + n_rays * 24
+    # algorithmic bytes of the march: 8 corners x 16 B (FP32) or 8 B (FP16)
+    # per Eq. 16 step, plus per ray 12 B of RGB out and 4 x 3 B of texels
+    per_step = 128 if wl["storage"] == "fp32" else 64
+    march_bytes = total_steps * per_step + n_rays * 24
     achieved = march_bytes / (ms_march * 1e-3) / 1e9
-    cpu = cpu_baseline(parts, cam, params, bg) if not args.no_cpu_baseline else None
+    kname = ("march_kernel" if wl["mode"] == "trace" else "march_batch_kernel") + \
+        f"<{wl['storage'].upper()}, EULER_PAPER, adaptive>"
+    cpu = None
+    if args.workload == "frame" and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, parts, cams[0], params, bg)
     line = {
-        "metric": METRIC,
+        "metric": wl["metric"],
         "value": round(world * n_rays / (ms_step * 1e-3) / 1e6, 3),
         "unit": "Mrays/s",
         "n_gpus": world,
@@ -267,14 +376,15 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f32" if wl["storage"] == "fp32" else "f32 (fp16 storage)",
         "data": "synthetic (seeded plume particles, checker+noise equirect background)",
-        "config": {"workload": WORKLOAD, "rays_per_step": n_rays, "rays_hit": hits,
-                   "march_steps_per_frame": total_steps,
+        "config": {"workload": wl["text"], "views": len(cams), "rays_per_step": n_rays,
+                   "rays_hit": hits, "march_steps_per_frame": total_steps,
                    "steps_per_hit_ray": round(total_steps / max(hits, 1), 2),
                    "march_ms": round(ms_march, 4),
                    "build_ms": round(ms_step - ms_march, 4),
                    "march_Mrays_s": round(n_rays / (ms_march * 1e-3) / 1e6, 3),
+                   "batch_config": tuned,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": None if args.no_e2e else {
@@ -283,13 +393,14 @@ def run_ours(args):
             "d2h_bytes_per_step": int(n_rays * 3 * 4)},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "march_kernel<FP32, EULER_PAPER, adaptive>",
-                     "peak_kind": peak_kind,
-                     "algorithmic_bytes": int(march_bytes)},
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic_for(args.workload), "kernel": kname,
+                     "peak_kind": peak_kind, "algorithmic_bytes": int(march_bytes)},
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
     }
+    if compare:
+        line["compare"] = compare
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -298,22 +409,25 @@ def run_ours(args):
 # --------------------------------------------------------------------------- #
 # the oracle (CPU baseline and reference arm)
 # --------------------------------------------------------------------------- #
-def oracle_frame_seconds(parts, cam, params, bg, frac: int, nthreads: int, full_vol=None):
+def oracle_frame_seconds(wl, parts, cam, params, bg, frac: int, nthreads: int, full_vol=None):
     """FP64 oracle time of one frame, measured on a 1/frac sample of each
     stage and scaled up: splat of every frac-th particle, Gladstone-Dale +
     gradient of a 1/frac slab of the grid, the march of every frac-th pixel
     (on the full oracle volume)."""
     import oracle
 
+    L = wl["L"]
+    dims = (L, L, L)
     t0 = time.perf_counter()
-    rho = oracle.splat(parts[::frac], DIMS, 2.0)
+    rho = oracle.splat(parts[::frac], dims, 2.0)
     t1 = time.perf_counter()
     slab = max(2, L // frac)
-    oracle.index_field(rho[:slab], float(np.float32(hi.K_GD)))
+    oracle.index_field(rho[:slab], K_GD32)
     t2 = time.perf_counter()
     if full_vol is None:
-        full_vol = oracle.index_field(oracle.splat(parts, DIMS, 2.0), float(np.float32(hi.K_GD)))
-    pix = np.arange(0, WIDTH * HEIGHT, frac, dtype=np.int64)
+        full_vol = oracle.index_field(oracle.splat(parts, dims, 2.0), K_GD32)
+    npx = cam["width"] * cam["height"]
+    pix = np.arange(0, npx, frac, dtype=np.int64)
     t3 = time.perf_counter()
     oracle.trace_grid(full_vol, cam, params, bg, pixels=pix, nthreads=nthreads)
     t4 = time.perf_counter()
@@ -321,14 +435,14 @@ def oracle_frame_seconds(parts, cam, params, bg, frac: int, nthreads: int, full_
     return per_frame, full_vol, (t1 - t0) + (t2 - t1) + (t4 - t3)
 
 
-def cpu_baseline(parts, cam, params, bg):
+def cpu_baseline(wl, parts, cam, params, bg):
     import oracle
 
     oracle.build()
     nthreads = os.cpu_count() or 1
-    frac = 1
-    sec, _, worked = oracle_frame_seconds(parts, cam, params, bg, frac, nthreads)
-    return {"value": round(WIDTH * HEIGHT / sec / 1e6, 4), "unit": "Mrays/s",
+    sec, _, worked = oracle_frame_seconds(wl, parts, cam, params, bg, 1, nthreads)
+    npx = cam["width"] * cam["height"]
+    return {"value": round(npx / sec / 1e6, 4), "unit": "Mrays/s",
             "cores": nthreads, "kind": "oracle",
             "sample": (f"one whole frame: all particles splatted (1 thread), the whole grid "
                        f"through Gladstone-Dale (1 thread), every pixel marched ({nthreads} "
@@ -343,24 +457,28 @@ def run_reference(args):
     import oracle
 
     oracle.build()
-    parts, cam, params, bg = scene()
+    wl = WORKLOADS["frame"]
+    dims, parts, cams, params, bg = scene(wl)
+    cam = cams[0]
     nthreads = os.cpu_count() or 1
     frac = 16
     full_vol = None
     times = []
     for k in range(args.warmup + args.steps):
-        sec, full_vol, _ = oracle_frame_seconds(parts, cam, params, bg, frac, nthreads, full_vol)
+        sec, full_vol, _ = oracle_frame_seconds(wl, parts, cam, params, bg, frac, nthreads,
+                                                full_vol)
         if k >= args.warmup:
             times.append(sec)
     ms = 1e3 * sum(times) / len(times)
-    value = round(WIDTH * HEIGHT / (ms * 1e-3) / 1e6, 4)
+    npx = cam["width"] * cam["height"]
+    value = round(npx / (ms * 1e-3) / 1e6, 4)
     sample = (f"per step 1/{frac} of each stage (every {frac}th particle, 1/{frac} of the grid, "
               f"every {frac}th pixel), scaled to one frame")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic", "config": {"workload": wl["text"]},
         "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": nthreads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0,
@@ -376,6 +494,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
+    ap.add_argument("--workload", default="frame", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the per-view and FP32 comparison marches (multi-view workloads)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

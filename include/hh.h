@@ -274,6 +274,81 @@ hh_status hh_batch_launch_graph(hh_batch b, void* stream);
 hh_status hh_batch_free(hh_batch b);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of render requests                         */
+/* ---------------------------------------------------------------------- */
+
+/* A render server for requests of 1..256 views against device-resident
+ * per-simulation-frame volumes (the paper's use: many cameras observing one
+ * shared, time-varying refractive volume, Sec. 1 and Sec. 4.2). A worker
+ * thread admits a request as soon as one of the server's slots is free and
+ * its output buffers fit in the server's device-memory budget; each
+ * admitted request runs as one persistent batched launch (hh_batch kernel,
+ * bit-identical to hh_trace) on its slot's stream, so requests arriving while
+ * others run overlap with them on the GPU. Requests that do not fit yet wait;
+ * later smaller ones may pass them unless they have waited over 200 ms. A
+ * request whose outputs exceed the whole budget is refused (HH_ERR_OOM).
+ * Requests for a frame not yet put wait for it. All host waits are bounded. */
+typedef struct hh_server_s* hh_server;
+
+/* Outputs a request asks for (rgb is always written). */
+#define HH_OUT_RGB 1   /* H*W*3 floats per view                         */
+#define HH_OUT_EXIT 2  /* exit_pos and exit_dir, H*W*3 floats each      */
+#define HH_OUT_STEPS 4 /* steps (int32) and flags (uint32), H*W each    */
+
+typedef struct {
+    uint64_t submitted, admitted, completed, cancelled, failed, rejected;
+    uint64_t pending, running;  /* now                                      */
+    uint64_t rays_completed;    /* primary rays of completed requests       */
+    size_t pool_used, pool_capacity; /* bytes of the output budget         */
+} hh_serve_stats;
+
+/* Creates a server on the current device with `mem_budget_bytes` of output
+ * memory (one cudaMalloc; HH_ERR_OOM if the device cannot provide it) and
+ * `max_slots` concurrent requests (1..64, one stream each). */
+hh_status hh_serve_create(size_t mem_budget_bytes, int max_slots, hh_server* out);
+
+/* Launch shape used for every request (see hh_batch_config). */
+hh_status hh_serve_set_config(hh_server s, const hh_batch_config* cfg);
+
+/* Registers the volume of simulation frame `frame_id` (the server borrows
+ * it: its build must have finished, and it must stay alive and unchanged
+ * while requests on it run; the server's streams do not wait for others). Replacing
+ * or removing a frame that is being rendered returns HH_ERR_BUSY. */
+hh_status hh_serve_put_volume(hh_server s, int64_t frame_id, hh_volume vol);
+hh_status hh_serve_remove_volume(hh_server s, int64_t frame_id);
+
+/* Queues a request of n_views cameras on frame `frame_id`; returns its
+ * ticket at once. `outputs` is a mask of HH_OUT_* bits. */
+hh_status hh_serve_submit(hh_server s, int64_t frame_id, const hh_camera* cams, int n_views,
+                          const hh_step_params* params, const hh_background* bg, int outputs,
+                          uint64_t* ticket);
+
+/* HH_OK (with the submit-to-completion latency in ms) when the request is
+ * done, HH_ERR_BUSY while it waits or runs, HH_ERR_CANCELLED,
+ * HH_ERR_NOT_FOUND for unknown or released tickets, HH_ERR_CUDA on failure. */
+hh_status hh_serve_poll(hh_server s, uint64_t ticket, double* latency_ms);
+
+/* As poll, but waits up to timeout_ms (HH_ERR_TIMEOUT when it runs out). */
+hh_status hh_serve_wait(hh_server s, uint64_t ticket, int timeout_ms, double* latency_ms);
+
+/* Device pointers of a done request's view outputs (inside the server's
+ * budget; valid until hh_serve_release). Pixel layout as hh_view_out. */
+hh_status hh_serve_view(hh_server s, uint64_t ticket, int view, hh_view_out* out);
+
+/* Frees a finished request's outputs and forgets its ticket; a waiting or
+ * running request returns HH_ERR_BUSY (cancel it first). */
+hh_status hh_serve_release(hh_server s, uint64_t ticket);
+
+/* Cancels a request: a waiting one at once, a running one when its launch
+ * ends (its result is discarded). Cancelled requests still need releasing. */
+hh_status hh_serve_cancel(hh_server s, uint64_t ticket);
+
+hh_status hh_serve_get_stats(hh_server s, hh_serve_stats* out);
+
+/* Stops the worker, waits for running launches and frees the server. */
+hh_status hh_serve_destroy(hh_server s);
+
+/* ---------------------------------------------------------------------- */
 /* Diagnostics                                                             */
 /* ---------------------------------------------------------------------- */
 

@@ -657,6 +657,47 @@ cudaError_t launch_trace(const hh_volume_s* vol, const hh_camera& cam, const hh_
 
 }  // namespace hh
 
+namespace hh {
+
+size_t view_record_bytes() { return sizeof(ViewArgs); }
+
+int build_view_table(const hh_camera* cams, const hh_view_out* outs, int n, int tile_w,
+                     void* host_records) {
+    ViewArgs* v = static_cast<ViewArgs*>(host_records);
+    const int tile_h = 32 / tile_w;
+    int64_t tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        v[i] = make_view_args(cams[i], outs[i], tile_w);
+        v[i].tile_begin = static_cast<int>(tiles);
+        tiles += static_cast<int64_t>(v[i].tiles_x) * ((cams[i].height + tile_h - 1) / tile_h);
+        if (tiles > (int64_t(1) << 30)) return -1;
+    }
+    return static_cast<int>(tiles);
+}
+
+cudaError_t launch_batch(const hh_volume_s* vol, const hh_step_params& P, const hh_background& bg,
+                         const void* views_dev, int n_views, int total_tiles, unsigned* counter,
+                         const hh_batch_config& cfg, int sm_count, cudaStream_t s) {
+    if (vol->layout != HH_LAYOUT_BRICK2) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    int bps = cfg.blocks_per_sm;
+    if (bps <= 0) {
+        dispatch<BatchOccupancy>(vol->storage, P.stepper, P.adaptive, cfg.block_threads,
+                                 (n_views + 1) * sizeof(int), &bps);
+        bps = max(bps, 1);
+    }
+    const VolArgs V = make_vol_args(vol, P, bg);
+    dispatch<BatchLaunch>(vol->storage, P.stepper, P.adaptive, V,
+                          static_cast<const ViewArgs*>(views_dev), n_views, total_tiles,
+                          cfg.tile_w, counter, cfg.refill_min, sm_count * bps, cfg.block_threads,
+                          s);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace hh
+
 // ------------------------------------------------------------------------
 // Batched multi-view launches (hh_batch_*)
 // ------------------------------------------------------------------------

@@ -74,6 +74,20 @@ class hh_batch_config(ctypes.Structure):
                 ("refill_min", ctypes.c_int), ("tile_w", ctypes.c_int)]
 
 
+class hh_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("pending", ctypes.c_uint64), ("running", ctypes.c_uint64),
+                ("rays_completed", ctypes.c_uint64), ("pool_used", ctypes.c_size_t),
+                ("pool_capacity", ctypes.c_size_t)]
+
+
+HH_OUT_RGB = 1
+HH_OUT_EXIT = 2
+HH_OUT_STEPS = 4
+
+
 # Every symbol include/hh.h declares, with (restype, argtypes).
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -108,6 +122,23 @@ SIGNATURES = {
     "hh_batch_launch": (ctypes.c_int, [_P, _P]),
     "hh_batch_launch_graph": (ctypes.c_int, [_P, _P]),
     "hh_batch_free": (ctypes.c_int, [_P]),
+    "hh_serve_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_P)]),
+    "hh_serve_set_config": (ctypes.c_int, [_P, ctypes.POINTER(hh_batch_config)]),
+    "hh_serve_put_volume": (ctypes.c_int, [_P, ctypes.c_int64, _P]),
+    "hh_serve_remove_volume": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "hh_serve_submit": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(hh_camera), ctypes.c_int,
+                                       ctypes.POINTER(hh_step_params),
+                                       ctypes.POINTER(hh_background), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_uint64)]),
+    "hh_serve_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "hh_serve_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "hh_serve_view": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int,
+                                     ctypes.POINTER(hh_view_out)]),
+    "hh_serve_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "hh_serve_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "hh_serve_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(hh_serve_stats)]),
+    "hh_serve_destroy": (ctypes.c_int, [_P]),
     "hh_last_error": (ctypes.c_char_p, []),
     "hh_kernel_launch_count": (ctypes.c_uint64, []),
 }
@@ -346,6 +377,117 @@ def hh_batch_launch_graph(b: Batch, stream=None):
 
 def hh_batch_free(b: Batch):
     b.close()
+
+
+class Server:
+    """Owns an hh_server handle."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+        self._keep = []  # volumes and backgrounds the server borrows
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(load().hh_serve_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle is not None and self.handle.value:
+                load().hh_serve_destroy(self.handle)
+        except Exception:
+            pass
+
+
+def hh_serve_create(mem_budget_bytes: int, max_slots: int) -> Server:
+    out = ctypes.c_void_p()
+    _check(load().hh_serve_create(int(mem_budget_bytes), int(max_slots), ctypes.byref(out)))
+    return Server(out)
+
+
+def hh_serve_set_config(s: Server, block_threads=128, blocks_per_sm=0, refill_min=32, tile_w=8):
+    c = hh_batch_config(int(block_threads), int(blocks_per_sm), int(refill_min), int(tile_w))
+    _check(load().hh_serve_set_config(s.handle, ctypes.byref(c)))
+
+
+def hh_serve_put_volume(s: Server, frame_id: int, vol: Volume):
+    _check(load().hh_serve_put_volume(s.handle, int(frame_id), vol.handle))
+    s._keep.append(vol)
+
+
+def hh_serve_remove_volume(s: Server, frame_id: int):
+    _check(load().hh_serve_remove_volume(s.handle, int(frame_id)))
+
+
+def hh_serve_submit(s: Server, frame_id: int, cams, params, bg, outputs: int = HH_OUT_RGB) -> int:
+    n = len(cams)
+    c_cams = (hh_camera * max(n, 1))(*[c if isinstance(c, hh_camera) else make_camera(c)
+                                       for c in cams])
+    P = params if isinstance(params, hh_step_params) else make_params(params)
+    B = hh_background(_ptr(bg), int(bg.shape[1]), int(bg.shape[0]))
+    t = ctypes.c_uint64()
+    _check(load().hh_serve_submit(s.handle, int(frame_id), c_cams, n, ctypes.byref(P),
+                                  ctypes.byref(B), int(outputs), ctypes.byref(t)))
+    s._keep.append(bg)
+    return int(t.value)
+
+
+def hh_serve_poll(s: Server, ticket: int):
+    """Returns (status, latency_ms); status HH_OK, HH_ERR_BUSY, ... (no raise
+    for BUSY)."""
+    lat = ctypes.c_double(0.0)
+    st = load().hh_serve_poll(s.handle, ctypes.c_uint64(ticket), ctypes.byref(lat))
+    return st, lat.value
+
+
+def hh_serve_wait(s: Server, ticket: int, timeout_ms: int = 10000) -> float:
+    lat = ctypes.c_double(0.0)
+    _check(load().hh_serve_wait(s.handle, ctypes.c_uint64(ticket), int(timeout_ms),
+                                ctypes.byref(lat)))
+    return lat.value
+
+
+class _DeviceArray:
+    """A __cuda_array_interface__ view of device memory owned elsewhere."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape),
+                                         "typestr": typestr, "version": 3, "strides": None}
+
+
+def hh_serve_view(s: Server, ticket: int, view: int, width: int, height: int) -> dict:
+    """Copies of a done request's view outputs as torch CUDA tensors."""
+    import torch
+
+    o = hh_view_out()
+    _check(load().hh_serve_view(s.handle, ctypes.c_uint64(ticket), int(view), ctypes.byref(o)))
+    npx = int(width) * int(height)
+    out = {}
+    for name, n, ts in (("rgb", npx * 3, "<f4"), ("exit_pos", npx * 3, "<f4"),
+                        ("exit_dir", npx * 3, "<f4"), ("steps", npx, "<i4"),
+                        ("flags", npx, "<i4")):
+        ptr = getattr(o, name)
+        if ptr:
+            out[name] = torch.as_tensor(_DeviceArray(ptr, (n,), ts), device="cuda").clone()
+    return out
+
+
+def hh_serve_release(s: Server, ticket: int):
+    _check(load().hh_serve_release(s.handle, ctypes.c_uint64(ticket)))
+
+
+def hh_serve_cancel(s: Server, ticket: int):
+    _check(load().hh_serve_cancel(s.handle, ctypes.c_uint64(ticket)))
+
+
+def hh_serve_get_stats(s: Server) -> dict:
+    st = hh_serve_stats()
+    _check(load().hh_serve_get_stats(s.handle, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in hh_serve_stats._fields_}
+
+
+def hh_serve_destroy(s: Server):
+    s.close()
 
 
 def hh_last_error() -> str:

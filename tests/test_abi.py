@@ -48,7 +48,11 @@ def test_struct_layouts_match_header(lib):
                "hh_step_params": ["stepper", "adaptive", "h_fixed", "h_min", "h_max", "theta_max",
                                   "eps", "max_steps"],
                "hh_background": ["rgb8_dev", "width", "height"],
-               "hh_view_out": ["rgb", "exit_pos", "exit_dir", "steps", "flags"]}
+               "hh_view_out": ["rgb", "exit_pos", "exit_dir", "steps", "flags"],
+               "hh_batch_config": ["block_threads", "blocks_per_sm", "refill_min", "tile_w"],
+               "hh_serve_stats": ["submitted", "admitted", "completed", "cancelled", "failed",
+                                  "rejected", "pending", "running", "rays_completed",
+                                  "pool_used", "pool_capacity"]}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
              "int main(void) {"]
     for s, fields in structs.items():

@@ -1,0 +1,18 @@
+"""CPU test of the render server's output-memory allocator (host logic of
+the serving path): compiles tests/native/pool_test.cpp against csrc/pool.h
+with g++ and runs it."""
+import os
+import subprocess
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_offset_pool(tmp_path):
+    exe = tmp_path / "pool_test"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I",
+                    os.path.join(ROOT, "paper_2603_02048_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "native", "pool_test.cpp"), "-o", str(exe)],
+                   check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "pool ok" in r.stdout
