@@ -80,6 +80,16 @@ WORKLOADS = {
 }
 
 
+SERVE = {
+    "L": 384, "particles": 1048576, "frames": 60, "duration_s": 2.0, "rates": (25, 50, 100, 200),
+    "metric": "serving Mrays/s with p50/p99 latency (Poisson requests of 1-16 views, 384^3 FP16)",
+    "text": ("60 device-resident 384^3 FP16 volumes of a drifting 1,048,576-particle plume "
+             "(one per sim frame, 30 Hz); Poisson arrivals over 2 s, each request 1-16 views "
+             "(uniform) at resolutions from {320x240, 1280x720, 1920x1080, 3840x2160}, eyes "
+             "1.5 grid widths away; continuous batching over 8 slot streams, 16 GiB output "
+             "budget; Eq. 16 adaptive, theta_max=3e-5")}
+
+
 def scene(wl: dict):
     L = wl["L"]
     dims = (L, L, L)
@@ -407,6 +417,126 @@ def run_ours(args):
 
 
 # --------------------------------------------------------------------------- #
+# serving
+# --------------------------------------------------------------------------- #
+def run_serve(args):
+    """Replays seeded Poisson request streams against the render server in
+    real time and reports throughput and latency percentiles per rate."""
+    import threading
+
+    import torch
+
+    from paper_2603_02048_gb300 import build as hb
+    from paper_2603_02048_gb300 import hh
+
+    hb.build()
+    hh.load()
+    dev = torch.device("cuda", 0)
+    L, nf = SERVE["L"], SERVE["frames"]
+    dims = (L, L, L)
+    params = f32(hi.params_euler_adaptive(dims, theta_max=hi.THETA_CALIBRATED))
+    bg_t = torch.from_numpy(hi.checker_background()).to(dev)
+    base = hi.plume_particles(SERVE["particles"], L)
+    grid = hh.make_grid(dims, 2.0, "fp16")
+    rho = torch.empty(L ** 3, device=dev)
+    vols = []
+    t0 = time.perf_counter()
+    for f in range(nf):
+        parts_t = torch.from_numpy(hi.drifting_plume_frame(base, f, L=L)).to(dev)
+        hh.hh_splat_density(parts_t, grid, rho)
+        vols.append(hh.hh_volume_from_density(rho, grid, K_GD32))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    del rho
+
+    srv = hh.hh_serve_create(16 << 30, 8)
+    # launch shape: autotuned once on a representative 8-view request of frame 0
+    probe = f32([hi.orbit_camera(dims, 45.0 * i, 10.0, *hi.SERVE_RESOLUTIONS[i % 4])
+                 for i in range(8)])
+    probe_outs = [{"rgb": torch.empty(c["width"] * c["height"] * 3, device=dev)} for c in probe]
+    b = hh.hh_batch_create(vols[0], probe, params, bg_t, probe_outs)
+    tuned = hh.hh_batch_autotune(b, reps=2)
+    b.close()
+    del probe_outs
+    hh.hh_serve_set_config(srv, **tuned)
+    for f, v in enumerate(vols):
+        hh.hh_serve_put_volume(srv, f, v)
+
+    def cams_of(req):
+        return f32([hi.orbit_camera(dims, az, el, w, h) for az, el, w, h in req["views"]])
+
+    # warm-up: a few requests through the whole path
+    for req in hi.serving_requests(rate_hz=50, duration_s=0.2, n_frames=nf, seed=99)[:4]:
+        t = hh.hh_serve_submit(srv, req["frame"], cams_of(req), params, bg_t)
+        hh.hh_serve_wait(srv, t, 60000)
+        hh.hh_serve_release(srv, t)
+
+    sweep = []
+    for rate in SERVE["rates"]:
+        reqs = hi.serving_requests(rate_hz=rate, duration_s=SERVE["duration_s"], n_frames=nf)
+        prepared = [(r["t"], r["frame"], cams_of(r)) for r in reqs]
+        tickets = []
+        lock = threading.Lock()
+        lat = []
+        rays = [0]
+
+        def collector():
+            i = 0
+            while True:
+                with lock:
+                    if i >= len(tickets):
+                        if len(tickets) == len(prepared):
+                            return
+                        tk = None
+                    else:
+                        tk, nr = tickets[i]
+                if tk is None:
+                    time.sleep(0.0005)
+                    continue
+                lat.append(hh.hh_serve_wait(srv, tk, 120000))
+                hh.hh_serve_release(srv, tk)
+                rays[0] += nr
+                i += 1
+
+        th = threading.Thread(target=collector)
+        th.start()
+        start = time.perf_counter()
+        for t_arr, frame, cams in prepared:
+            delay = start + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tk = hh.hh_serve_submit(srv, frame, cams, params, bg_t)
+            with lock:
+                tickets.append((tk, sum(c["width"] * c["height"] for c in cams)))
+        th.join()
+        wall = time.perf_counter() - start
+        lat_a = np.array(lat)
+        offered = sum(sum(c["width"] * c["height"] for c in cams) for _, _, cams in prepared)
+        sweep.append({"rate_req_s": rate, "requests": len(prepared),
+                      "offered_Mrays_s": round(offered / SERVE["duration_s"] / 1e6, 1),
+                      "Mrays_s": round(rays[0] / wall / 1e6, 1),
+                      "p50_ms": round(float(np.percentile(lat_a, 50)), 2),
+                      "p99_ms": round(float(np.percentile(lat_a, 99)), 2),
+                      "max_ms": round(float(lat_a.max()), 2),
+                      "wall_s": round(wall, 3)})
+    stats = hh.hh_serve_get_stats(srv)
+    srv.close()
+    for v in vols:
+        v.close()
+    top = sweep[-1]
+    print(json.dumps({
+        "metric": SERVE["metric"], "value": top["Mrays_s"], "unit": "Mrays/s", "n_gpus": 1,
+        "steps": len(SERVE["rates"]), "warmup": 4, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (fp16 storage)", "data": "synthetic (seeded drifting plume, Poisson)",
+        "config": {"workload": SERVE["text"], "volume_build_s_60_frames": round(build_s, 2),
+                   "batch_config": tuned},
+        "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"], "sweep": sweep,
+        "server_stats": {k: int(v) for k, v in stats.items()},
+    }), flush=True)
+
+
+# --------------------------------------------------------------------------- #
 # the oracle (CPU baseline and reference arm)
 # --------------------------------------------------------------------------- #
 def oracle_frame_seconds(wl, parts, cam, params, bg, frac: int, nthreads: int, full_vol=None):
@@ -494,13 +624,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
-    ap.add_argument("--workload", default="frame", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="frame", choices=sorted(WORKLOADS) + ["serve"])
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the per-view and FP32 comparison marches (multi-view workloads)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 
