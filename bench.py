@@ -121,7 +121,8 @@ def dist_setup(n_gpus):
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl" if _cuda() else "gloo")
+        backend = os.environ.get("HH_DIST_BACKEND") or ("nccl" if _cuda() else "gloo")
+        dist.init_process_group(backend)
         return dist, int(os.environ["RANK"]), world, int(os.environ.get("LOCAL_RANK", "0"))
     return None, 0, 1, 0
 
