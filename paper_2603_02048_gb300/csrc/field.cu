@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(256) field_column_kernel(const float* __restri
         const bool xl = i > 0, xh = i < nx - 1, yl = j > 0, yh = j < ny - 1;
         float dprev = k0 > 0 ? K * __ldg(col + (k0 - 1) * sz) : 0.0f;
         float dcur = K * __ldg(col + k0 * sz);
+#pragma unroll 4
         for (int k = k0; k < k1; ++k) {
             const float* c = col + k * sz;
             const float dnext = (k + 1 < nz) ? K * __ldg(c + sz) : 0.0f;

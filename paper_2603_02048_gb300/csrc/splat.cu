@@ -2,14 +2,14 @@
 // rho(x_v) = sum_p m_p W(|x_v - x_p|, h) at voxel centres, W the M4 cubic
 // spline with support 2h.
 //
-// One warp per particle. The lanes form an 8 (x) by 4 (y) grid that walks the
-// particle's footprint (the voxels whose centres lie within 2h on every axis:
-// 8^3 for h = 2) one z slice and four rows at a time, so a warp's atomics
-// cover four 8-float rows (four 32-byte sectors) and compile to
-// fire-and-forget reductions in L2. dz^2 and dy^2 are hoisted out of the
-// inner loop, indices are 32-bit (grids hold fewer than 2^31 voxels) and
-// voxels beyond the support (r^2 >= 4h^2, about half of the footprint box)
-// skip the square root and the atomic.
+// One warp per particle. Each lane owns an (x, y) column of the particle's
+// footprint (the voxels whose centres lie within 2h on every axis: 8^3 for
+// h = 2), the lanes forming an 8 (x) by 4 (y) grid, and walks the column in
+// z with the column's squared distance computed once; at every z slice a
+// warp's atomics cover four 8-float rows (four 32-byte sectors) and compile
+// to fire-and-forget reductions in L2. Columns and voxels beyond the support
+// (r^2 >= 4h^2, about half of the footprint box) skip the square root and the
+// atomic; indices are 32-bit (grids hold fewer than 2^31 voxels).
 #include "hh_internal.h"
 
 namespace hh {
@@ -58,24 +58,25 @@ __global__ void __launch_bounds__(256) splat_warp_kernel(const float4* __restric
     const int lx = lane & 7, ly = lane >> 3;
     const float reach2 = 4.0f * h * h;
     const float m = q.w;
-    for (int k = z0; k <= z1; ++k) {
-        const float dz = (static_cast<float>(k) + 0.5f) - q.z;
-        const float dz2 = dz * dz;
-        if (!(dz2 < reach2)) continue;  // warp-uniform: the slice is outside the support
-        const unsigned plane = static_cast<unsigned>(k) * static_cast<unsigned>(ny);
-        for (int jb = y0; jb <= y1; jb += 4) {
-            const int j = jb + ly;
+    const int ez = z1 - z0 + 1;
+    const unsigned plane = static_cast<unsigned>(nx) * static_cast<unsigned>(ny);
+    const float dz0 = (static_cast<float>(z0) + 0.5f) - q.z;
+    for (int yb = y0; yb <= y1; yb += 4) {
+        for (int xb = x0; xb <= x1; xb += 8) {
+            const int i = xb + lx, j = yb + ly;
+            if (i > x1 || j > y1) continue;
+            const float dx = (static_cast<float>(i) + 0.5f) - q.x;
             const float dy = (static_cast<float>(j) + 0.5f) - q.y;
-            const float dyz2 = fmaf(dy, dy, dz2);
-            float* row = rho + (plane + static_cast<unsigned>(min(j, y1))) * static_cast<unsigned>(nx);
-            const bool row_ok = j <= y1 && dyz2 < reach2;
-            for (int ib = x0; ib <= x1; ib += 8) {
-                const int i = ib + lx;
-                const float dx = (static_cast<float>(i) + 0.5f) - q.x;
-                const float r2 = fmaf(dx, dx, dyz2);
-                if (row_ok && i <= x1 && r2 < reach2) {
+            const float dxy2 = fmaf(dx, dx, dy * dy);
+            if (!(dxy2 < reach2)) continue;  // the whole column is outside the support
+            float* col = rho + (static_cast<unsigned>(z0) * static_cast<unsigned>(ny) +
+                                static_cast<unsigned>(j)) * static_cast<unsigned>(nx) + i;
+            float dz = dz0;  // (k + 1/2) - z exactly: each +1 is exact at these magnitudes
+            for (int k = 0; k < ez; ++k, dz += 1.0f, col += plane) {
+                const float r2 = fmaf(dz, dz, dxy2);
+                if (r2 < reach2) {
                     const float w = m4_kernel(sqrt_approx(r2), inv_h, norm);
-                    if (w > 0.0f) atomicAdd(row + i, m * w);
+                    if (w > 0.0f) atomicAdd(col, m * w);
                 }
             }
         }
