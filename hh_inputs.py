@@ -234,3 +234,49 @@ def params_euler_adaptive(dims, theta_max: float = 3e-5, h_min: float = 0.125,
 # calibrated to the 256^3 plume so that Eq. 18 actually varies the step.
 THETA_PAPER = 3e-3
 THETA_CALIBRATED = 3e-5
+
+
+# --------------------------------------------------------------------------- #
+# scene geometry and homogeneous turbulence
+# --------------------------------------------------------------------------- #
+def checker_texture(W: int = 256, H: int = 256, squares: int = 8, seed: int = SEED_BACKGROUND,
+                    tint=(1.0, 1.0, 1.0)) -> np.ndarray:
+    """RGB8 checkerboard texture (levels 0.15 / 0.85, U[-0.05, 0.05] noise)."""
+    g = rng(seed + 101)
+    j = np.arange(H)[:, None]
+    i = np.arange(W)[None, :]
+    base = np.where(((i * squares // W) + (j * squares // H)) % 2 == 0, 0.15, 0.85)
+    img = base[:, :, None] * np.asarray(tint)[None, None, :] + g.uniform(-0.05, 0.05, (H, W, 3))
+    return np.ascontiguousarray(np.clip(np.rint(img * 255.0), 0, 255), dtype=np.uint8)
+
+
+def boards_behind(dims, depths=(0.5, 1.5), size=1.2) -> list:
+    """Checkerboard planes facing a camera on the -x side, at x = nx +
+    depth * nx, centred on the grid axis, size * nx wide: the 'two boards at
+    different distances' of the paper's depth experiment (Sec. 4.2)."""
+    nx, ny, nz = dims
+    out = []
+    for k, dpt in enumerate(depths):
+        half = 0.5 * size * nx * (1.0 + dpt)
+        out.append({"origin": [nx + dpt * nx, ny / 2 - half, nz / 2 - half],
+                    "u": [0.0, 2 * half, 0.0], "v": [0.0, 0.0, 2 * half],
+                    "tex": checker_texture(256, 256, squares=8 + 4 * k, seed=10 + k,
+                                           tint=(1.0, 0.9 - 0.2 * k, 0.8))})
+    return out
+
+
+def homogeneous_turbulence_dn(dims, seed: int = SEED_SCENE, sigma: float = 2.0,
+                              std: float = 1e-5) -> np.ndarray:
+    """Statistically homogeneous dn field: white noise filtered by a Gaussian
+    of width sigma voxels in Fourier space (periodic, so homogeneous up to the
+    faces), scaled to standard deviation `std`. FP32, (nz, ny, nx)."""
+    g = rng(seed)
+    nx, ny, nz = dims
+    noise = g.standard_normal((nz, ny, nx))
+    kz = np.fft.fftfreq(nz)[:, None, None]
+    ky = np.fft.fftfreq(ny)[None, :, None]
+    kx = np.fft.rfftfreq(nx)[None, None, :]
+    filt = np.exp(-2.0 * (np.pi * sigma) ** 2 * (kx ** 2 + ky ** 2 + kz ** 2))
+    field = np.fft.irfftn(np.fft.rfftn(noise) * filt, s=(nz, ny, nx), axes=(0, 1, 2))
+    field *= std / field.std()
+    return np.ascontiguousarray(field, dtype=np.float32)

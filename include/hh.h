@@ -105,13 +105,33 @@ typedef struct {
     int max_steps;    /* >= 0 steps inside the box per ray                   */
 } hh_step_params;
 
-/* Equirectangular RGB8 background (device), row-major H x W x 3, row 0 at the
- * +z pole. Colour of direction d: phi = atan2(d_y, d_x), theta = polar angle
- * from +z, u = (phi/2pi + 1/2) W - 1/2, v = theta/pi H - 1/2, bilinear over
- * texel centres, u wrapping, v clamped; value/255. */
+/* A textured rectangle of the scene behind or around the volume (the
+ * paper's scene geometry, Sec. 4.1, in its simplest analytic form): points
+ * origin + a u + b v with a, b in [0, 1]; u and v must be perpendicular and
+ * non-zero. Its RGB8 texture (device, row-major H x W x 3, row 0 at b = 0) is
+ * sampled bilinearly at (a W - 1/2, b H - 1/2), clamped to the texel
+ * centres. Two-sided and opaque. */
+typedef struct {
+    float origin[3], u[3], v[3]; /* voxel units */
+    const uint8_t* rgb8_dev;
+    int width, height;           /* >= 2 each */
+} hh_plane;
+
+#define HH_MAX_PLANES 4
+
+/* What a ray sees once it is straight again (after leaving the volume, or
+ * from the eye when it misses it): the nearest of n_planes planes it hits in
+ * front of it (t > 0), otherwise the equirectangular RGB8 environment map
+ * (device, row-major H x W x 3, row 0 at the +z pole). Map colour of
+ * direction d: phi = atan2(d_y, d_x), theta = polar angle from +z,
+ * u = (phi/2pi + 1/2) W - 1/2, v = theta/pi H - 1/2, bilinear over texel
+ * centres, u wrapping, v clamped; value/255. Planes are seen by the exit ray
+ * only: the scene lies outside the refractive volume. */
 typedef struct {
     const uint8_t* rgb8_dev;
-    int width, height; /* width >= 1, height >= 2 */
+    int width, height;  /* width >= 1, height >= 2 */
+    int n_planes;       /* 0 .. HH_MAX_PLANES */
+    hh_plane planes[HH_MAX_PLANES];
 } hh_background;
 
 /* Per-view outputs (device, caller-owned), pixel-major in row order. rgb is

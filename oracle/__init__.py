@@ -71,6 +71,18 @@ class _Camera(ctypes.Structure):
                 ("width", ctypes.c_int), ("height", ctypes.c_int)]
 
 
+class _Plane(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("u", ctypes.c_double * 3),
+                ("v", ctypes.c_double * 3), ("rgb8", ctypes.POINTER(ctypes.c_uint8)),
+                ("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+class _Scene(ctypes.Structure):
+    _fields_ = [("rgb8", ctypes.POINTER(ctypes.c_uint8)), ("width", ctypes.c_int),
+                ("height", ctypes.c_int), ("n_planes", ctypes.c_int),
+                ("planes", _Plane * 4)]
+
+
 _D = ctypes.POINTER(ctypes.c_double)
 _F = ctypes.POINTER(ctypes.c_float)
 
@@ -96,8 +108,8 @@ def _load():
         lib.hho_slab.argtypes = [_D, _D, _D, _D, _D]
         lib.hho_background.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int,
                                        ctypes.c_int, _D, _D]
-        trace_args = [ctypes.POINTER(_Camera), ctypes.POINTER(_Params),
-                      ctypes.POINTER(ctypes.c_uint8), ctypes.c_int, ctypes.c_int,
+        lib.hho_scene_color.argtypes = [ctypes.POINTER(_Scene), _D, _D, _D]
+        trace_args = [ctypes.POINTER(_Camera), ctypes.POINTER(_Params), ctypes.POINTER(_Scene),
                       ctypes.POINTER(ctypes.c_int64), ctypes.c_int64, _D, _D, _D,
                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint32),
                       ctypes.c_int]
@@ -270,11 +282,44 @@ def march_rays(field: dict, box, C0: np.ndarray, w0: np.ndarray, params: dict,
     return {"exit_pos": ep, "exit_dir": ed, "steps": steps, "flags": flags}
 
 
-def _trace(fn, lead_args, cam, params, bg, pixels, nthreads):
+class _SceneHolder:
+    """A C scene over the environment map and up to 4 textured planes
+    (dicts {origin, u, v, tex (H, W, 3) uint8}); keeps the arrays alive."""
+
+    def __init__(self, bg: np.ndarray, planes=None):
+        self.arrays = [np.ascontiguousarray(bg, dtype=np.uint8)]
+        self.s = _Scene()
+        H, W, _ = self.arrays[0].shape
+        self.s.rgb8 = _ptr(self.arrays[0], ctypes.c_uint8)
+        self.s.width, self.s.height = W, H
+        planes = list(planes or [])
+        assert len(planes) <= 4
+        self.s.n_planes = len(planes)
+        for k, pl in enumerate(planes):
+            tex = np.ascontiguousarray(pl["tex"], dtype=np.uint8)
+            self.arrays.append(tex)
+            p = self.s.planes[k]
+            p.origin[:] = [float(x) for x in pl["origin"]]
+            p.u[:] = [float(x) for x in pl["u"]]
+            p.v[:] = [float(x) for x in pl["v"]]
+            p.rgb8 = _ptr(tex, ctypes.c_uint8)
+            p.height, p.width = tex.shape[0], tex.shape[1]
+
+
+def scene_color(bg: np.ndarray, P, d, planes=None) -> np.ndarray:
+    """What the straight ray P + t d (t > 0) sees: nearest plane, else the map."""
+    sc = _SceneHolder(bg, planes)
+    P, d = _vec3(P), _vec3(d)
+    out = np.zeros(3)
+    _load().hho_scene_color(ctypes.byref(sc.s), _ptr(P, ctypes.c_double),
+                            _ptr(d, ctypes.c_double), _ptr(out, ctypes.c_double))
+    return out
+
+
+def _trace(fn, lead_args, cam, params, bg, pixels, nthreads, planes=None):
     c = _camera(cam)
     P = _params(params)
-    bg = np.ascontiguousarray(bg, dtype=np.uint8)
-    bgH, bgW, _ = bg.shape
+    sc = _SceneHolder(bg, planes)
     if pixels is None:
         n = int(cam["width"]) * int(cam["height"])
         pix_ptr = None
@@ -287,7 +332,7 @@ def _trace(fn, lead_args, cam, params, bg, pixels, nthreads):
     ed = np.zeros((n, 3))
     steps = np.zeros(n, dtype=np.int32)
     flags = np.zeros(n, dtype=np.uint32)
-    fn(*lead_args, ctypes.byref(c), ctypes.byref(P), _ptr(bg, ctypes.c_uint8), bgW, bgH,
+    fn(*lead_args, ctypes.byref(c), ctypes.byref(P), ctypes.byref(sc.s),
        pix_ptr, n, _ptr(rgb, ctypes.c_double), _ptr(ep, ctypes.c_double),
        _ptr(ed, ctypes.c_double), _ptr(steps, ctypes.c_int32), _ptr(flags, ctypes.c_uint32),
        int(nthreads))
@@ -295,7 +340,7 @@ def _trace(fn, lead_args, cam, params, bg, pixels, nthreads):
 
 
 def trace_grid(vol4: np.ndarray, cam: dict, params: dict, bg: np.ndarray, pixels=None,
-               nthreads: int = 1) -> dict:
+               nthreads: int = 1, planes=None) -> dict:
     """Traces camera pixels through a gridded {dn, g} volume (nz, ny, nx, 4).
 
     Returns per-pixel arrays rgb (n,3), exit_pos (n,3), exit_dir (n,3),
@@ -304,15 +349,15 @@ def trace_grid(vol4: np.ndarray, cam: dict, params: dict, bg: np.ndarray, pixels
     vol4 = np.ascontiguousarray(vol4, dtype=np.float64)
     nz, ny, nx, _ = vol4.shape
     return _trace(_load().hho_trace_grid, (_ptr(vol4, ctypes.c_double), nx, ny, nz), cam,
-                  params, bg, pixels, nthreads)
+                  params, bg, pixels, nthreads, planes)
 
 
 def trace_field(field: dict, box, cam: dict, params: dict, bg: np.ndarray, pixels=None,
-                nthreads: int = 1) -> dict:
+                nthreads: int = 1, planes=None) -> dict:
     """Traces camera pixels through an analytic (or gridded) field in box [0, box]."""
     holder = _FieldHolder(field)
     box = _vec3(box)
     out = _trace(_load().hho_trace_field, (ctypes.byref(holder.f), _ptr(box, ctypes.c_double)),
-                 cam, params, bg, pixels, nthreads)
+                 cam, params, bg, pixels, nthreads, planes)
     del holder
     return out

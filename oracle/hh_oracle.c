@@ -504,8 +504,81 @@ void hho_background(const uint8_t* rgb8, int W, int H, const double d[3], double
     }
 }
 
+/*
+ * Scene geometry behind the volume (the paper's scene intersection, Sec. 4.1,
+ * in its simplest analytic form): textured rectangles origin + a u + b v,
+ * a, b in [0, 1], u perpendicular to v; RGB8 texture row 0 at b = 0, sampled
+ * bilinearly at (a W - 1/2, b H - 1/2) clamped to the texel centres. The
+ * straight ray P + t d, t > 0, shows the nearest rectangle it hits, else the
+ * environment map.
+ */
+typedef struct {
+    double origin[3], u[3], v[3];
+    const uint8_t* rgb8;
+    int width, height;
+} hho_plane;
+
+typedef struct {
+    const uint8_t* rgb8; /* environment map */
+    int width, height;
+    int n_planes;
+    hho_plane planes[4];
+} hho_scene;
+
+static void texture_bilinear(const uint8_t* tex, int W, int H, double s, double t, double rgb[3]) {
+    if (s < 0.0) s = 0.0;
+    if (s > W - 1) s = W - 1;
+    if (t < 0.0) t = 0.0;
+    if (t > H - 1) t = H - 1;
+    long i0 = (long)floor(s), j0 = (long)floor(t);
+    if (i0 > W - 2) i0 = W - 2;
+    if (j0 > H - 2) j0 = H - 2;
+    double fs = s - (double)i0, ft = t - (double)j0;
+    for (int c = 0; c < 3; ++c) {
+        double t00 = tex[((size_t)j0 * W + i0) * 3 + c] / 255.0;
+        double t01 = tex[((size_t)j0 * W + i0 + 1) * 3 + c] / 255.0;
+        double t10 = tex[((size_t)(j0 + 1) * W + i0) * 3 + c] / 255.0;
+        double t11 = tex[((size_t)(j0 + 1) * W + i0 + 1) * 3 + c] / 255.0;
+        rgb[c] = (1.0 - ft) * ((1.0 - fs) * t00 + fs * t01) + ft * ((1.0 - fs) * t10 + fs * t11);
+    }
+}
+
+void hho_scene_color(const hho_scene* S, const double P[3], const double d[3], double rgb[3]) {
+    double best_t = INFINITY, best_a = 0.0, best_b = 0.0;
+    int best = -1;
+    for (int k = 0; k < S->n_planes; ++k) {
+        const hho_plane* pl = &S->planes[k];
+        double nrm[3], op[3], X[3], r[3];
+        cross3(pl->u, pl->v, nrm);
+        double den = dot3(d, nrm);
+        if (den == 0.0) continue;
+        for (int a = 0; a < 3; ++a) op[a] = pl->origin[a] - P[a];
+        double t = dot3(op, nrm) / den;
+        if (!(t > 0.0) || !(t < best_t)) continue;
+        for (int a = 0; a < 3; ++a) {
+            X[a] = P[a] + t * d[a];
+            r[a] = X[a] - pl->origin[a];
+        }
+        double aa = dot3(r, pl->u) / dot3(pl->u, pl->u);
+        double bb = dot3(r, pl->v) / dot3(pl->v, pl->v);
+        if (aa >= 0.0 && aa <= 1.0 && bb >= 0.0 && bb <= 1.0) {
+            best = k;
+            best_t = t;
+            best_a = aa;
+            best_b = bb;
+        }
+    }
+    if (best < 0) {
+        hho_background(S->rgb8, S->width, S->height, d, rgb);
+        return;
+    }
+    const hho_plane* pl = &S->planes[best];
+    texture_bilinear(pl->rgb8, pl->width, pl->height, best_a * pl->width - 0.5,
+                     best_b * pl->height - 0.5, rgb);
+}
+
 /* ------------------------------------------------------------------------- */
-/* Whole pixels: ray generation -> entry -> march -> background               */
+/* Whole pixels: ray generation -> entry -> march -> scene                    */
 /* ------------------------------------------------------------------------- */
 
 typedef struct {
@@ -513,8 +586,7 @@ typedef struct {
     double box[3];
     const hho_camera* cam;
     const hho_params* P;
-    const uint8_t* bg;
-    int bgW, bgH;
+    const hho_scene* scene;
     const int64_t* pixels;
     int64_t n_pix;
     double* rgb;
@@ -550,7 +622,7 @@ static void trace_pixel(const trace_job* J, int64_t slot, int64_t pix) {
         }
     }
     double rgb[3];
-    hho_background(J->bg, J->bgW, J->bgH, ed, rgb);
+    hho_scene_color(J->scene, ep, ed, rgb);
     for (int a = 0; a < 3; ++a) {
         if (J->rgb) J->rgb[3 * slot + a] = rgb[a];
         if (J->exit_pos) J->exit_pos[3 * slot + a] = ep[a];
@@ -568,13 +640,14 @@ static void* trace_worker(void* arg) {
 }
 
 /*
- * Traces the pixels of one camera through a field. pixels == NULL traces all
+ * Traces the pixels of one camera through a field and into the scene.
+ * pixels == NULL traces all
  * width*height pixels in row-major order; otherwise output slot s holds
  * pixel pixels[s] (= py*width + px). Outputs may be NULL. Work is striped
  * over nthreads POSIX threads (each pixel is independent). Returns 0.
  */
 int hho_trace_field(const hho_field* F, const double box[3], const hho_camera* cam,
-                    const hho_params* P, const uint8_t* bg, int bgW, int bgH,
+                    const hho_params* P, const hho_scene* scene,
                     const int64_t* pixels, int64_t n_pix, double* rgb, double* exit_pos,
                     double* exit_dir, int32_t* steps, uint32_t* flags, int nthreads) {
     if (!pixels) n_pix = (int64_t)cam->width * cam->height;
@@ -588,9 +661,7 @@ int hho_trace_field(const hho_field* F, const double box[3], const hho_camera* c
         for (int a = 0; a < 3; ++a) J->box[a] = box[a];
         J->cam = cam;
         J->P = P;
-        J->bg = bg;
-        J->bgW = bgW;
-        J->bgH = bgH;
+        J->scene = scene;
         J->pixels = pixels;
         J->n_pix = n_pix;
         J->rgb = rgb;
@@ -612,7 +683,7 @@ int hho_trace_field(const hho_field* F, const double box[3], const hho_camera* c
 
 /* Grid convenience: the box is [0,nx] x [0,ny] x [0,nz] over vol4. */
 int hho_trace_grid(const double* vol4, int nx, int ny, int nz, const hho_camera* cam,
-                   const hho_params* P, const uint8_t* bg, int bgW, int bgH,
+                   const hho_params* P, const hho_scene* scene,
                    const int64_t* pixels, int64_t n_pix, double* rgb, double* exit_pos,
                    double* exit_dir, int32_t* steps, uint32_t* flags, int nthreads) {
     hho_field F;
@@ -623,7 +694,7 @@ int hho_trace_grid(const double* vol4, int nx, int ny, int nz, const hho_camera*
     F.dims[2] = nz;
     F.vol4 = vol4;
     double box[3] = {nx, ny, nz};
-    return hho_trace_field(&F, box, cam, P, bg, bgW, bgH, pixels, n_pix, rgb, exit_pos, exit_dir,
+    return hho_trace_field(&F, box, cam, P, scene, pixels, n_pix, rgb, exit_pos, exit_dir,
                            steps, flags, nthreads);
 }
 

@@ -147,6 +147,29 @@ hh_status check_params(const hh_step_params* P) {
     return HH_OK;
 }
 
+hh_status check_background(const hh_background* bg) {
+    if (!bg || !bg->rgb8_dev || bg->width < 1 || bg->height < 2)
+        return fail(HH_ERR_INVALID_ARG, "background needs a device pointer, width >= 1, height >= 2");
+    if (bg->n_planes < 0 || bg->n_planes > HH_MAX_PLANES)
+        return fail(HH_ERR_INVALID_ARG, "n_planes must be in [0, %d]", HH_MAX_PLANES);
+    for (int k = 0; k < bg->n_planes; ++k) {
+        const hh_plane& p = bg->planes[k];
+        if (!p.rgb8_dev || p.width < 2 || p.height < 2)
+            return fail(HH_ERR_INVALID_ARG, "plane %d needs a device texture of at least 2 x 2", k);
+        float uu = 0.0f, vv = 0.0f, uv = 0.0f;
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(p.origin[a]) || !std::isfinite(p.u[a]) || !std::isfinite(p.v[a]))
+                return fail(HH_ERR_INVALID_ARG, "plane %d: non-finite vector", k);
+            uu += p.u[a] * p.u[a];
+            vv += p.v[a] * p.v[a];
+            uv += p.u[a] * p.v[a];
+        }
+        if (!(uu > 0.0f) || !(vv > 0.0f) || std::fabs(uv) > 1e-4f * std::sqrt(uu * vv))
+            return fail(HH_ERR_INVALID_ARG, "plane %d: u and v must be non-zero and perpendicular", k);
+    }
+    return HH_OK;
+}
+
 hh_status check_camera(const hh_camera& c, int i) {
     if (c.width < 1 || c.height < 1 || c.width > 65536 || c.height > 65536 ||
         static_cast<int64_t>(c.width) * c.height > (int64_t(1) << 31))
@@ -298,8 +321,7 @@ hh_status hh_trace(hh_volume vol, const hh_camera* cams, int n_cams,
     if (n_cams > 0 && (!cams || !outs)) return fail(HH_ERR_INVALID_ARG, "cameras/outputs NULL");
     hh_status st = check_params(params);
     if (st != HH_OK) return st;
-    if (!bg || !bg->rgb8_dev || bg->width < 1 || bg->height < 2)
-        return fail(HH_ERR_INVALID_ARG, "background needs a device pointer, width >= 1, height >= 2");
+    if ((st = check_background(bg)) != HH_OK) return st;
     for (int i = 0; i < n_cams; ++i) {
         if ((st = check_camera(cams[i], i)) != HH_OK) return st;
         if (!outs[i].rgb) return fail(HH_ERR_INVALID_ARG, "view %d: rgb output is NULL", i);

@@ -60,6 +60,7 @@ hh_status ok();
 // Argument checks shared by the trace entry points (defined in api.cpp).
 hh_status check_params(const hh_step_params* P);
 hh_status check_camera(const hh_camera& c, int i);
+hh_status check_background(const hh_background* bg);
 
 // Kernel launchers. Each returns the launch status (cudaGetLastError()).
 cudaError_t launch_splat(const float4* xyzm, int64_t n, int nx, int ny, int nz, float h,

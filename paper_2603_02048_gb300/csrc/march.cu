@@ -55,6 +55,8 @@ struct VolArgs {
     int max_steps;
     const uint8_t* bg;
     int bgW, bgH;
+    int n_planes;
+    hh_plane planes[HH_MAX_PLANES];
 };
 
 // View-side arguments: the camera, the caller's output buffers and the
@@ -264,9 +266,9 @@ __device__ __forceinline__ float3 renormalize(float3 wr, float3 d1) {
     return fma3(rm1, wr + d1, d1);
 }
 
-// Colour of direction d in the equirect background (bilinear, u wraps,
+// Colour of direction d in the equirect environment map (bilinear, u wraps,
 // v clamps; value / 255).
-__device__ __forceinline__ float3 background(const VolArgs& A, float3 d) {
+__device__ __forceinline__ float3 environment(const VolArgs& A, float3 d) {
     const float phi = atan2f(d.y, d.x);
     const float theta = atan2f(sqrtf(d.x * d.x + d.y * d.y), d.z);
     const float W = static_cast<float>(A.bgW), H = static_cast<float>(A.bgH);
@@ -290,6 +292,69 @@ __device__ __forceinline__ float3 background(const VolArgs& A, float3 d) {
         out[c] = lerpf(lerpf(t00, t01, fu), lerpf(t10, t11, fu), fv) * (1.0f / 255.0f);
     }
     return make_float3(out[0], out[1], out[2]);
+}
+
+__device__ __forceinline__ float3 f3(const float v[3]) { return make_float3(v[0], v[1], v[2]); }
+
+// Bilinear RGB8 texture lookup at texel coordinates (s, t), clamped to the
+// texel centres; value / 255.
+__device__ __forceinline__ float3 texel_bilinear(const uint8_t* tex, int W, int H, float s,
+                                                 float t) {
+    s = fminf(fmaxf(s, 0.0f), static_cast<float>(W - 1));
+    t = fminf(fmaxf(t, 0.0f), static_cast<float>(H - 1));
+    const int i0 = min(static_cast<int>(floorf(s)), W - 2);
+    const int j0 = min(static_cast<int>(floorf(t)), H - 2);
+    const float fs = s - static_cast<float>(i0), ft = t - static_cast<float>(j0);
+    const uint8_t* r0 = tex + (static_cast<size_t>(j0) * W + i0) * 3;
+    const uint8_t* r1 = r0 + static_cast<size_t>(W) * 3;
+    float out[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float t00 = __ldg(r0 + c), t01 = __ldg(r0 + 3 + c);
+        const float t10 = __ldg(r1 + c), t11 = __ldg(r1 + 3 + c);
+        out[c] = lerpf(lerpf(t00, t01, fs), lerpf(t10, t11, fs), ft) * (1.0f / 255.0f);
+    }
+    return make_float3(out[0], out[1], out[2]);
+}
+
+// What the straight ray P + t d (t > 0) sees: the nearest textured plane it
+// hits, else the environment map.
+// A call, not inlined: it runs once per ray, and keeping its registers out of
+// the step loop's allocation is as fast as inlining it (measured).
+__device__ __noinline__ float3 scene_color(const VolArgs& A, float3 P, float3 d) {
+    float best_t = INFINITY, best_a = 0.0f, best_b = 0.0f;
+    int best = -1;
+#pragma unroll
+    for (int k = 0; k < HH_MAX_PLANES; ++k) {
+        if (k >= A.n_planes) break;
+        const hh_plane& pl = A.planes[k];
+        const float3 o = f3(pl.origin), u = f3(pl.u), v = f3(pl.v);
+        const float3 nrm = cross(u, v);
+        const float den = dot(d, nrm);
+        if (den == 0.0f) continue;
+        const float t = dot(o - P, nrm) / den;
+        if (!(t > 0.0f) || !(t < best_t)) continue;
+        const float3 r = fma3(t, d, P) - o;
+        const float a = dot(r, u) / dot(u, u), b = dot(r, v) / dot(v, v);
+        if (a >= 0.0f && a <= 1.0f && b >= 0.0f && b <= 1.0f) {
+            best = k;
+            best_t = t;
+            best_a = a;
+            best_b = b;
+        }
+    }
+    if (best < 0) return environment(A, d);
+    const uint8_t* tex = A.planes[0].rgb8_dev;
+    int W = A.planes[0].width, H = A.planes[0].height;
+#pragma unroll
+    for (int k = 1; k < HH_MAX_PLANES; ++k)
+        if (best == k) {
+            tex = A.planes[k].rgb8_dev;
+            W = A.planes[k].width;
+            H = A.planes[k].height;
+        }
+    return texel_bilinear(tex, W, H, best_a * static_cast<float>(W) - 0.5f,
+                          best_b * static_cast<float>(H) - 0.5f);
 }
 
 // Ray through the centre of pixel (px, py); row 0 at the top.
@@ -479,7 +544,7 @@ __device__ __forceinline__ void ray_end(const VolArgs& V, const ViewArgs& C, int
         ep = R.c;
         ed = R.wr + R.d;
     }
-    const float3 rgb = background(V, ed);
+    const float3 rgb = scene_color(V, ep, ed);
     const size_t pix = static_cast<size_t>(py) * C.W + px;
     C.rgb[3 * pix + 0] = rgb.x;
     C.rgb[3 * pix + 1] = rgb.y;
@@ -677,6 +742,8 @@ VolArgs make_vol_args(const hh_volume_s* vol, const hh_step_params& P, const hh_
     A.bg = bg.rgb8_dev;
     A.bgW = bg.width;
     A.bgH = bg.height;
+    A.n_planes = bg.n_planes;
+    for (int k = 0; k < HH_MAX_PLANES; ++k) A.planes[k] = bg.planes[k];
     return A;
 }
 
@@ -871,8 +938,7 @@ hh_status hh_batch_create(hh_volume vol, const hh_camera* cams, int n_cams,
         return fail(HH_ERR_INVALID_ARG, "a batch needs 1 to 4096 cameras and outputs");
     hh_status st = hh::check_params(params);
     if (st != HH_OK) return st;
-    if (!bg || !bg->rgb8_dev || bg->width < 1 || bg->height < 2)
-        return fail(HH_ERR_INVALID_ARG, "background needs a device pointer, width >= 1, height >= 2");
+    if ((st = hh::check_background(bg)) != HH_OK) return st;
     for (int i = 0; i < n_cams; ++i) {
         if ((st = hh::check_camera(cams[i], i)) != HH_OK) return st;
         if (!outs[i].rgb) return fail(HH_ERR_INVALID_ARG, "view %d: rgb output is NULL", i);

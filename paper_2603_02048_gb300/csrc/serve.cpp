@@ -316,8 +316,7 @@ hh_status hh_serve_submit(hh_server S, int64_t frame_id, const hh_camera* cams, 
         return hh::fail(HH_ERR_INVALID_ARG, "unknown output bits");
     hh_status st = hh::check_params(params);
     if (st != HH_OK) return st;
-    if (!bg || !bg->rgb8_dev || bg->width < 1 || bg->height < 2)
-        return hh::fail(HH_ERR_INVALID_ARG, "background needs a device pointer, width >= 1, height >= 2");
+    if ((st = hh::check_background(bg)) != HH_OK) return st;
     Request r;
     for (int i = 0; i < n_views; ++i) {
         if ((st = hh::check_camera(cams[i], i)) != HH_OK) return st;

@@ -58,9 +58,19 @@ class hh_step_params(ctypes.Structure):
                 ("eps", ctypes.c_float), ("max_steps", ctypes.c_int)]
 
 
+class hh_plane(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("u", ctypes.c_float * 3),
+                ("v", ctypes.c_float * 3), ("rgb8_dev", ctypes.c_void_p),
+                ("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+HH_MAX_PLANES = 4
+
+
 class hh_background(ctypes.Structure):
     _fields_ = [("rgb8_dev", ctypes.c_void_p), ("width", ctypes.c_int),
-                ("height", ctypes.c_int)]
+                ("height", ctypes.c_int), ("n_planes", ctypes.c_int),
+                ("planes", hh_plane * HH_MAX_PLANES)]
 
 
 class hh_view_out(ctypes.Structure):
@@ -211,6 +221,35 @@ def make_params(p: dict) -> hh_step_params:
                           float(p.get("eps", 1e-6)), int(p["max_steps"]))
 
 
+def make_background(bg, planes=None) -> hh_background:
+    """bg: (H, W, 3) uint8 CUDA tensor (environment map); planes: list of
+    dicts {origin, u, v, tex ((h, w, 3) uint8 CUDA tensor)}."""
+    B = hh_background()
+    B.rgb8_dev = _ptr(bg).value
+    B.width, B.height = int(bg.shape[1]), int(bg.shape[0])
+    planes = list(planes or [])
+    if len(planes) > HH_MAX_PLANES:
+        raise ValueError("too many planes")
+    B.n_planes = len(planes)
+    for k, pl in enumerate(planes):
+        P = B.planes[k]
+        P.origin[:] = [float(x) for x in pl["origin"]]
+        P.u[:] = [float(x) for x in pl["u"]]
+        P.v[:] = [float(x) for x in pl["v"]]
+        P.rgb8_dev = _ptr(pl["tex"]).value
+        P.height, P.width = int(pl["tex"].shape[0]), int(pl["tex"].shape[1])
+    return B
+
+
+def _background(bg) -> hh_background:
+    """A ready hh_background, a (map, planes) pair, or a map tensor alone."""
+    if isinstance(bg, hh_background):
+        return bg
+    if isinstance(bg, tuple):
+        return make_background(*bg)
+    return make_background(bg)
+
+
 class Volume:
     """Owns an hh_volume handle; freed on close() or garbage collection."""
 
@@ -296,7 +335,8 @@ def hh_volume_free(vol: Volume):
 
 def hh_trace(vol: Volume, cams, params, bg, outs, stream=None):
     """cams: list of camera dicts or hh_camera; params: dict or hh_step_params;
-    bg: (H, W, 3) uint8 CUDA tensor; outs: list of dicts with CUDA tensors
+    bg: (H, W, 3) uint8 CUDA tensor, (map, planes) or an hh_background (the
+    tensors must stay alive until the work is done); outs: list of dicts with CUDA tensors
     'rgb' (required) and optional 'exit_pos', 'exit_dir', 'steps', 'flags'."""
     n = len(cams)
     c_cams = (hh_camera * max(n, 1))(*[c if isinstance(c, hh_camera) else make_camera(c)
@@ -305,7 +345,7 @@ def hh_trace(vol: Volume, cams, params, bg, outs, stream=None):
         hh_view_out(_ptr(o["rgb"]), _ptr(o.get("exit_pos")), _ptr(o.get("exit_dir")),
                     _ptr(o.get("steps")), _ptr(o.get("flags"))) for o in outs])
     P = params if isinstance(params, hh_step_params) else make_params(params)
-    B = hh_background(_ptr(bg), int(bg.shape[1]), int(bg.shape[0]))
+    B = _background(bg)
     _check(load().hh_trace(vol.handle, c_cams, n, ctypes.byref(P), ctypes.byref(B), c_outs,
                            _stream(stream)))
 
@@ -343,7 +383,7 @@ def _views(cams, outs):
 def hh_batch_create(vol: Volume, cams, params, bg, outs) -> Batch:
     n, c_cams, c_outs = _views(cams, outs)
     P = params if isinstance(params, hh_step_params) else make_params(params)
-    B = hh_background(_ptr(bg), int(bg.shape[1]), int(bg.shape[0]))
+    B = _background(bg)
     out = ctypes.c_void_p()
     _check(load().hh_batch_create(vol.handle, c_cams, n, ctypes.byref(P), ctypes.byref(B),
                                   c_outs, ctypes.byref(out)))
@@ -424,7 +464,7 @@ def hh_serve_submit(s: Server, frame_id: int, cams, params, bg, outputs: int = H
     c_cams = (hh_camera * max(n, 1))(*[c if isinstance(c, hh_camera) else make_camera(c)
                                        for c in cams])
     P = params if isinstance(params, hh_step_params) else make_params(params)
-    B = hh_background(_ptr(bg), int(bg.shape[1]), int(bg.shape[0]))
+    B = _background(bg)
     t = ctypes.c_uint64()
     _check(load().hh_serve_submit(s.handle, int(frame_id), c_cams, n, ctypes.byref(P),
                                   ctypes.byref(B), int(outputs), ctypes.byref(t)))

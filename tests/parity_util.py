@@ -45,8 +45,9 @@ def f32(x):
 
 
 def gpu_trace(hh, torch, vol, cams, params, bg_t, want_all=True):
-    """Traces cams through vol on the GPU; returns a list of numpy dicts."""
-    dev = bg_t.device
+    """Traces cams through vol on the GPU; returns a list of numpy dicts.
+    bg_t: the environment map tensor, or (map, planes)."""
+    dev = (bg_t[0] if isinstance(bg_t, tuple) else bg_t).device
     outs = []
     for c in cams:
         n = c["width"] * c["height"]

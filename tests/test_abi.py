@@ -47,7 +47,8 @@ def test_struct_layouts_match_header(lib):
                "hh_camera": ["eye", "look_at", "up", "vfov_deg", "width", "height"],
                "hh_step_params": ["stepper", "adaptive", "h_fixed", "h_min", "h_max", "theta_max",
                                   "eps", "max_steps"],
-               "hh_background": ["rgb8_dev", "width", "height"],
+               "hh_background": ["rgb8_dev", "width", "height", "n_planes", "planes"],
+               "hh_plane": ["origin", "u", "v", "rgb8_dev", "width", "height"],
                "hh_view_out": ["rgb", "exit_pos", "exit_dir", "steps", "flags"],
                "hh_batch_config": ["block_threads", "blocks_per_sm", "refill_min", "tile_w"],
                "hh_serve_stats": ["submitted", "admitted", "completed", "cancelled", "failed",

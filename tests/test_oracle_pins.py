@@ -551,3 +551,87 @@ def test_march_rays_equals_single_rays(oracle_lib):
         np.testing.assert_array_equal(many["exit_pos"][i], one["exit_pos"])
         np.testing.assert_array_equal(many["exit_dir"][i], one["exit_dir"])
         assert many["steps"][i] == one["steps"] and many["flags"][i] == one["flags"]
+
+
+# --------------------------------------------------------------------------- #
+# Scene planes (the analytic scene geometry behind the volume)
+# --------------------------------------------------------------------------- #
+def _ramp_texture(W=64, H=32):
+    t = np.zeros((H, W, 3), dtype=np.uint8)
+    t[..., 0] = np.arange(W)[None, :] * 4
+    t[..., 1] = np.arange(H)[:, None] * 8
+    t[..., 2] = 200
+    return t
+
+
+def test_plane_hit_texture_coordinates(oracle_lib):
+    """A ramp texture returns its bilinear texel coordinates: the hit point
+    (solved here as a 3x3 linear system P + t d = o + a u + b v) maps to
+    (a W - 1/2, b H - 1/2), clamped to the texel centres."""
+    W, H = 64, 32
+    tex = _ramp_texture(W, H)
+    plane = {"origin": [10.0, -20.0, 5.0], "u": [0.0, 40.0, 0.0], "v": [0.0, 0.0, 20.0],
+             "tex": tex}
+    env = np.full((8, 16, 3), 9, dtype=np.uint8)
+    r = np.random.default_rng(2)
+    for _ in range(40):
+        P = r.uniform(-50, 0, size=3)
+        X = np.array(plane["origin"]) + r.uniform(0.02, 0.98) * np.array(plane["u"]) \
+            + r.uniform(0.02, 0.98) * np.array(plane["v"])
+        d = (X - P) / np.linalg.norm(X - P)
+        A = np.column_stack([d, -np.array(plane["u"]), -np.array(plane["v"])])
+        t, a, b = np.linalg.solve(A, np.array(plane["origin"]) - P)
+        c = oracle_lib.scene_color(env, P, d, [plane]) * 255
+        s = min(max(a * W - 0.5, 0), W - 1)
+        q = min(max(b * H - 0.5, 0), H - 1)
+        assert c[0] == pytest.approx(4 * s, abs=1e-9) and c[1] == pytest.approx(8 * q, abs=1e-9)
+        assert c[2] == pytest.approx(200, abs=1e-9)
+
+
+def test_plane_nearest_front_and_misses(oracle_lib):
+    env = np.full((8, 16, 3), 9, dtype=np.uint8)
+    red = np.zeros((4, 4, 3), np.uint8)
+    red[..., 0] = 255
+    green = np.zeros((4, 4, 3), np.uint8)
+    green[..., 1] = 255
+    near = {"origin": [10.0, -5.0, -5.0], "u": [0.0, 10.0, 0.0], "v": [0.0, 0.0, 10.0],
+            "tex": red}
+    far = {"origin": [20.0, -5.0, -5.0], "u": [0.0, 10.0, 0.0], "v": [0.0, 0.0, 10.0],
+           "tex": green}
+    sc = oracle_lib.scene_color
+    np.testing.assert_allclose(sc(env, [0, 0, 0], [1, 0, 0], [far, near]), [1, 0, 0])
+    np.testing.assert_allclose(sc(env, [15, 0, 0], [1, 0, 0], [far, near]), [0, 1, 0])
+    np.testing.assert_allclose(sc(env, [0, 0, 0], [-1, 0, 0], [far, near]), 9 / 255)  # behind
+    np.testing.assert_allclose(sc(env, [0, 0, 0], [0, 1, 0], [far, near]), 9 / 255)  # parallel
+    np.testing.assert_allclose(sc(env, [0, 6, 0], [1, 0, 0], [far, near]), 9 / 255)  # beside
+
+
+def _slab_variance(oracle_lib, Lz, seeds=range(8), n_side=32):
+    """Mean squared exit deflection of parallel rays crossing a slab of
+    homogeneous turbulence (FFT-filtered noise, correlation 2 voxels) of
+    thickness Lz along +z."""
+    dims = (64, 64, Lz)
+    defl = []
+    for s in seeds:
+        dn = hi.homogeneous_turbulence_dn(dims, seed=100 + s, sigma=2.0)
+        vol = oracle_lib.index_field(dn.astype(np.float64), 1.0)
+        xs = np.linspace(1.0, 63.0, n_side)
+        X, Y = np.meshgrid(xs, xs)
+        C0 = np.c_[X.ravel(), Y.ravel(), np.zeros(X.size)]
+        w0 = np.tile([0.0, 0.0, 1.0], (X.size, 1))
+        P = {"stepper": "rk4", "adaptive": False, "h_fixed": 0.5, "max_steps": 10 * Lz}
+        out = oracle_lib.march_rays({"kind": "grid", "vol4": vol}, dims, C0, w0, P, nthreads=8)
+        assert np.all(out["flags"] == oracle_lib.FLAG_EXITED)
+        defl.append(out["exit_dir"][:, :2])
+    d = np.concatenate(defl)
+    return float(np.mean(np.sum(d * d, axis=1)))
+
+
+def test_angle_of_arrival_variance_grows_linearly_with_path(oracle_lib):
+    """Eq. 19: under constant turbulence strength the angle-of-arrival
+    variance grows linearly with the path length L (<alpha^2> = 3/8 K_n^2 L).
+    The marched deflection of parallel rays through homogeneous turbulence
+    doubles when the slab thickness doubles."""
+    v = [_slab_variance(oracle_lib, L) for L in (24, 48, 96)]
+    assert v[0] > 0
+    assert 1.75 < v[1] / v[0] < 2.3 and 1.75 < v[2] / v[1] < 2.3, v
