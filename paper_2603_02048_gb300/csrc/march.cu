@@ -27,6 +27,7 @@
 // 2x2x2 micro-bricks (BRICK2), which spreads the distinct voxels of a warp's
 // corner load over all L1 bank groups.
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <string>
@@ -62,8 +63,9 @@ struct VolArgs {
 // View-side arguments: the camera, the caller's output buffers and the
 // view's place in a batch's tile list.
 struct ViewArgs {
-    float3 eye, look, up;
-    float vfov_deg;
+    float3 eye;
+    float3 f, r, u;    // camera basis: forward, right, up (computed on the host in FP64)
+    float a0, b0, s;   // pixel (x, y) -> a = a0 + (x + 1/2) s, b = b0 - (y + 1/2) s
     int W, H;
     float* rgb;
     float* exit_pos;
@@ -258,11 +260,15 @@ __device__ __forceinline__ float step_length(const VolArgs& A, float n, float gp
 }
 
 // Eq. 16's normalize, in deflection form: returns d' with w_ref + d' the unit
-// vector along w_ref + d1 (taking |w_ref| = 1).
+// vector along w_ref + d1 (taking |w_ref| = 1): w_ref + d' = (1 + r)(w_ref + d1)
+// with 1 + r = (1 + e)^(-1/2), e = |w_ref + d1|^2 - 1 = 2 w_ref.d1 + |d1|^2.
+// r is the Taylor polynomial -e/2 + 3e^2/8 - 5e^3/16 (error 35 e^4 / 128):
+// e is the squared turn of one step plus the previous rounding (below 1e-5
+// when Eq. 18 bounds the turn by theta_max <= 3e-3), and an error in r only
+// scales the length of w, never its direction, and is undone at the next step.
 __device__ __forceinline__ float3 renormalize(float3 wr, float3 d1) {
-    const float e = 2.0f * dot(wr, d1) + dot(d1, d1);
-    const float s = sqrt_approx(1.0f + e);
-    const float rm1 = __fdividef(-e, s * (1.0f + s));
+    const float e = fmaf(2.0f, dot(wr, d1), dot(d1, d1));
+    const float rm1 = e * fmaf(e, fmaf(-0.3125f, e, 0.375f), -0.5f);
     return fma3(rm1, wr + d1, d1);
 }
 
@@ -357,16 +363,14 @@ __device__ __noinline__ float3 scene_color(const VolArgs& A, float3 P, float3 d)
                           best_b * static_cast<float>(H) - 0.5f);
 }
 
-// Ray through the centre of pixel (px, py); row 0 at the top.
+// Ray through the centre of pixel (px, py); row 0 at the top:
+// normalize(f + a r + b u) with a = (2 (x + 1/2) / W - 1) t W / H and
+// b = (1 - 2 (y + 1/2) / H) t, t = tan(vfov / 2), i.e. a = a0 + (x + 1/2) s,
+// b = b0 - (y + 1/2) s with s = 2 t / H, a0 = -t W / H, b0 = t.
 __device__ __forceinline__ float3 primary_ray(const ViewArgs& A, int px, int py) {
-    const float3 f = normalized(A.look - A.eye);
-    const float3 r = normalized(cross(f, A.up));
-    const float3 u = cross(r, f);
-    const float t = tanf(0.5f * A.vfov_deg * (kPi / 180.0f));
-    const float W = static_cast<float>(A.W), H = static_cast<float>(A.H);
-    const float a = (2.0f * (static_cast<float>(px) + 0.5f) / W - 1.0f) * t * (W / H);
-    const float b = (1.0f - 2.0f * (static_cast<float>(py) + 0.5f) / H) * t;
-    return normalized(fma3(b, u, fma3(a, r, f)));
+    const float a = fmaf(static_cast<float>(px) + 0.5f, A.s, A.a0);
+    const float b = fmaf(static_cast<float>(py) + 0.5f, -A.s, A.b0);
+    return normalized(fma3(b, A.u, fma3(a, A.r, A.f)));
 }
 
 // Slab test of o + t d against [0,nx]x[0,ny]x[0,nz]; hit iff
@@ -750,9 +754,29 @@ VolArgs make_vol_args(const hh_volume_s* vol, const hh_step_params& P, const hh_
 ViewArgs make_view_args(const hh_camera& cam, const hh_view_out& out, int tile_w) {
     ViewArgs C;
     C.eye = make_float3(cam.eye[0], cam.eye[1], cam.eye[2]);
-    C.look = make_float3(cam.look_at[0], cam.look_at[1], cam.look_at[2]);
-    C.up = make_float3(cam.up[0], cam.up[1], cam.up[2]);
-    C.vfov_deg = cam.vfov_deg;
+    // camera basis and pixel mapping, once per view in FP64 (see primary_ray)
+    double f[3], r[3], u[3], fn = 0.0, rn = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        f[a] = static_cast<double>(cam.look_at[a]) - cam.eye[a];
+        fn += f[a] * f[a];
+    }
+    for (int a = 0; a < 3; ++a) f[a] /= std::sqrt(fn);
+    const double up[3] = {cam.up[0], cam.up[1], cam.up[2]};
+    r[0] = f[1] * up[2] - f[2] * up[1];
+    r[1] = f[2] * up[0] - f[0] * up[2];
+    r[2] = f[0] * up[1] - f[1] * up[0];
+    for (int a = 0; a < 3; ++a) rn += r[a] * r[a];
+    for (int a = 0; a < 3; ++a) r[a] /= std::sqrt(rn);
+    u[0] = r[1] * f[2] - r[2] * f[1];
+    u[1] = r[2] * f[0] - r[0] * f[2];
+    u[2] = r[0] * f[1] - r[1] * f[0];
+    C.f = make_float3(static_cast<float>(f[0]), static_cast<float>(f[1]), static_cast<float>(f[2]));
+    C.r = make_float3(static_cast<float>(r[0]), static_cast<float>(r[1]), static_cast<float>(r[2]));
+    C.u = make_float3(static_cast<float>(u[0]), static_cast<float>(u[1]), static_cast<float>(u[2]));
+    const double t = std::tan(0.5 * static_cast<double>(cam.vfov_deg) * (M_PI / 180.0));
+    C.a0 = static_cast<float>(-t * cam.width / cam.height);
+    C.b0 = static_cast<float>(t);
+    C.s = static_cast<float>(2.0 * t / cam.height);
     C.W = cam.width;
     C.H = cam.height;
     C.rgb = out.rgb;
