@@ -8,22 +8,42 @@
 // z with the column's squared distance computed once; at every z slice a
 // warp's atomics cover four 8-float rows (four 32-byte sectors) and compile
 // to fire-and-forget reductions in L2. Columns and voxels beyond the support
-// (r^2 >= 4h^2, about half of the footprint box) skip the square root and the
-// atomic; indices are 32-bit (grids hold fewer than 2^31 voxels).
+// (r^2 >= 4h^2, about half of the footprint box) skip the atomic; indices are
+// 32-bit (grids hold fewer than 2^31 voxels). The kernel is evaluated in r
+// with the particle's mass folded into its coefficients, and a column of
+// exactly 8 voxels (every interior particle when h = 2) is walked fully
+// unrolled.
 #include "hh_internal.h"
 
 namespace hh {
 namespace {
 
-// M4 cubic spline, q = r / h: norm (1 - 3/2 q^2 + 3/4 q^3) on [0,1),
-// norm (2 - q)^3 / 4 on [1,2), 0 beyond; norm = 1 / (pi h^3). Both pieces are
-// evaluated and selected, so lanes on either side of q = 1 do not diverge.
-__device__ __forceinline__ float m4_kernel(float r, float inv_h, float norm) {
-    const float q = r * inv_h;
-    const float inner = fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f);
-    const float t = fmaxf(2.0f - q, 0.0f);
-    const float outer = 0.25f * t * t * t;
-    return norm * (q < 1.0f ? inner : outer);
+// m W(r, h) for the M4 cubic spline with the particle mass folded in:
+// W = norm (1 - 3/2 q^2 + 3/4 q^3) on q = r/h < 1, norm (2 - q)^3 / 4 on
+// [1, 2), norm = 1 / (pi h^3); in r: m W = mn + r^2 (c2 + c3 r) for r < h and
+// d (2h - r)^3 beyond, mn = m norm, c2 = -3/2 mn / h^2, c3 = 3/4 mn / h^3,
+// d = mn / (4 h^3). Both pieces are evaluated and selected (no divergence).
+struct M4Coef {
+    float mn, c2, c3, d, h, two_h;
+};
+
+__device__ __forceinline__ M4Coef m4_coef(float m, float h, float inv_h, float norm) {
+    M4Coef c;
+    c.mn = m * norm;
+    const float inv_h2 = inv_h * inv_h, inv_h3 = inv_h2 * inv_h;
+    c.c2 = -1.5f * c.mn * inv_h2;
+    c.c3 = 0.75f * c.mn * inv_h3;
+    c.d = 0.25f * c.mn * inv_h3;
+    c.h = h;
+    c.two_h = 2.0f * h;
+    return c;
+}
+
+__device__ __forceinline__ float m4_mass(const M4Coef& c, float r2, float r) {
+    const float inner = fmaf(r2, fmaf(c.c3, r, c.c2), c.mn);
+    const float t = fmaxf(c.two_h - r, 0.0f);
+    const float outer = c.d * (t * t * t);
+    return r < c.h ? inner : outer;
 }
 
 // Hardware approximate square root (PTX sqrt.approx.f32, ~1 ulp).
@@ -57,7 +77,7 @@ __global__ void __launch_bounds__(256) splat_warp_kernel(const float4* __restric
     if (x1 < x0 || y1 < y0 || z1 < z0) return;
     const int lx = lane & 7, ly = lane >> 3;
     const float reach2 = 4.0f * h * h;
-    const float m = q.w;
+    const M4Coef cf = m4_coef(q.w, h, inv_h, norm);
     const int ez = z1 - z0 + 1;
     const unsigned plane = static_cast<unsigned>(nx) * static_cast<unsigned>(ny);
     const float dz0 = (static_cast<float>(z0) + 0.5f) - q.z;
@@ -69,14 +89,20 @@ __global__ void __launch_bounds__(256) splat_warp_kernel(const float4* __restric
             const float dy = (static_cast<float>(j) + 0.5f) - q.y;
             const float dxy2 = fmaf(dx, dx, dy * dy);
             if (!(dxy2 < reach2)) continue;  // the whole column is outside the support
-            float* col = rho + (static_cast<unsigned>(z0) * static_cast<unsigned>(ny) +
-                                static_cast<unsigned>(j)) * static_cast<unsigned>(nx) + i;
-            float dz = dz0;  // (k + 1/2) - z exactly: each +1 is exact at these magnitudes
-            for (int k = 0; k < ez; ++k, dz += 1.0f, col += plane) {
-                const float r2 = fmaf(dz, dz, dxy2);
-                if (r2 < reach2) {
-                    const float w = m4_kernel(sqrt_approx(r2), inv_h, norm);
-                    if (w > 0.0f) atomicAdd(col, m * w);
+            unsigned v = (static_cast<unsigned>(z0) * static_cast<unsigned>(ny) +
+                          static_cast<unsigned>(j)) * static_cast<unsigned>(nx) + i;
+            if (ez == 8) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k, v += plane) {
+                    const float dz = dz0 + static_cast<float>(k);  // exact at these magnitudes
+                    const float r2 = fmaf(dz, dz, dxy2);
+                    if (r2 < reach2) atomicAdd(rho + v, m4_mass(cf, r2, sqrt_approx(r2)));
+                }
+            } else {
+                float dz = dz0;  // (k + 1/2) - z exactly: each +1 is exact at these magnitudes
+                for (int k = 0; k < ez; ++k, dz += 1.0f, v += plane) {
+                    const float r2 = fmaf(dz, dz, dxy2);
+                    if (r2 < reach2) atomicAdd(rho + v, m4_mass(cf, r2, sqrt_approx(r2)));
                 }
             }
         }
