@@ -52,10 +52,10 @@ hh_status check_grid(const hh_grid* g, bool need_h) {
                     g->ny, g->nz, kMaxAxis);
     if (g->storage != HH_STORE_FP32 && g->storage != HH_STORE_FP16_SCALED)
         return fail(HH_ERR_INVALID_ARG, "unknown storage %d", g->storage);
-    if (static_cast<size_t>((g->nx + 1) / 2) * ((g->ny + 1) / 2) * ((g->nz + 1) / 2) * 8 >
+    if (static_cast<size_t>(brick2_count(g->nx)) * brick2_count(g->ny) * brick2_count(g->nz) * 8 >
         (size_t(1) << 31))
-        return fail(HH_ERR_INVALID_ARG, "grid %d x %d x %d: more than 2^31 voxels", g->nx, g->ny,
-                    g->nz);
+        return fail(HH_ERR_INVALID_ARG, "grid %d x %d x %d: more than 2^31 stored voxels", g->nx,
+                    g->ny, g->nz);
     if (need_h && !(g->h_kernel > 0.0f && std::isfinite(g->h_kernel)))
         return fail(HH_ERR_INVALID_ARG, "h_kernel must be a positive finite number");
     return HH_OK;
@@ -84,13 +84,13 @@ hh_status new_volume(const hh_grid* g, hh_volume* out) {
     v->storage = g->storage;
     v->h_kernel = g->h_kernel;
     v->layout = HH_LAYOUT_BRICK2;
-    v->bx = static_cast<unsigned>((g->nx + 1) / 2);
-    v->bxy = v->bx * static_cast<unsigned>((g->ny + 1) / 2);
-    const size_t padded = static_cast<size_t>(v->bxy) * ((g->nz + 1) / 2) * 8;
+    v->bx = brick2_count(g->nx);
+    v->bxy = v->bx * brick2_count(g->ny);
+    const size_t padded = static_cast<size_t>(v->bxy) * brick2_count(g->nz) * 8;
     v->bytes = padded * (g->storage == HH_STORE_FP32 ? 16 : 8);
     cudaGetDevice(&v->device);
     cudaError_t e = cudaMalloc(&v->data, v->bytes);
-    if (e == cudaSuccess) e = cudaMemset(v->data, 0, v->bytes);  // padding voxels read as 0
+    if (e == cudaSuccess) e = cudaMemset(v->data, 0, v->bytes);  // even-padding voxels read as 0
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&v->scales_dev), 2 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&v->max_dev), 2 * sizeof(unsigned));
     if (e != cudaSuccess) {

@@ -6,12 +6,13 @@
 //   FP16: four halves, 8 B/voxel, dn / s_n and g / s_g with per-volume scales
 //         s = max|.| / 16384 (pass 1 reduces the maxima, pass 2 recomputes the
 //         differences and quantises; rho is read twice, nothing else stored).
-// Threads map to (x, y) columns in 32x8 tiles and walk 16 z slices each, so
-// every load of rho is coalesced, the z neighbours come from registers and
-// the x/y neighbours from L1.
-// The packed volume is written in the volume's layout (BRICK2 for volumes the
-// march reads, LINEAR for the allocation-free build's caller buffer); in
-// BRICK2 the x-pairs of a warp land in whole 32-byte sectors.
+// Threads map to (x, y) columns, x fastest (a warp is 32 consecutive
+// columns), and walk 16 z slices each, so every load of rho is coalesced, the
+// z neighbours come from registers and the x/y neighbours from L1.
+// The packed volume is written in the volume's layout (BRICK2 with its halo
+// of edge copies for volumes the march reads, LINEAR for the allocation-free
+// build's caller buffer); in BRICK2 the x-pairs of a warp land in whole
+// 32-byte sectors.
 #include "hh_internal.h"
 
 namespace hh {
@@ -26,9 +27,10 @@ struct OutLayout {
     unsigned bx, bxy;
 };
 
+// Element of grid voxel (i, j, k) in the output layout (BRICK2: halo offset).
 __device__ __forceinline__ size_t out_index(const OutLayout& L, int i, int j, int k, int nx,
                                             int ny) {
-    if (L.layout == HH_LAYOUT_BRICK2) return brick2_offset(i, j, k, L.bx, L.bxy);
+    if (L.layout == HH_LAYOUT_BRICK2) return brick2_offset(i + 1, j + 1, k + 1, L.bx, L.bxy);
     return (static_cast<size_t>(k) * ny + j) * nx + i;
 }
 
@@ -43,27 +45,35 @@ __device__ __forceinline__ float scale_of(unsigned bits) {
 #define FIELD_ZRUN 16
 
 template <int MODE>  // 0: FP32 store, 1: FP16 max pass, 2: FP16 store
-__global__ void __launch_bounds__(256) field_column_kernel(const float* __restrict__ rho, int nx,
+__global__ void __launch_bounds__(256, MODE == 2 ? 5 : 8) field_column_kernel(const float* __restrict__ rho, int nx,
                                                            int ny, int nz, float K, OutLayout L,
                                                            void* __restrict__ out,
                                                            unsigned* __restrict__ max_bits,
                                                            float* __restrict__ scales) {
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * 8 + threadIdx.y;
-    const int k0 = blockIdx.z * FIELD_ZRUN;
+    // Threads cover the stored (x, y) columns (I, J), x fastest, 256 per block
+    // (a warp is 32 consecutive columns, wrapping across rows). With the
+    // BRICK2 halo (h = 1, stores only) every stored column, halo included, is
+    // written by its own thread with the values of grid column (clamp(I - 1),
+    // clamp(J - 1)), the halo's copy of the nearest edge column; the z halo
+    // slices repeat the first and last grid slice.
+    const int h = (MODE != 1 && L.layout == HH_LAYOUT_BRICK2) ? 1 : 0;
+    const int W = nx + 2 * h, Hh = ny + 2 * h;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = t / W, I = t - J * W;
+    const int k0 = blockIdx.y * FIELD_ZRUN;
     const int k1 = min(k0 + FIELD_ZRUN, nz);
     float s_n = 1.0f, s_g = 1.0f;
     if (MODE == 2) {
         s_n = scale_of(max_bits[0]);
         s_g = scale_of(max_bits[1]);
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 &&
-        threadIdx.y == 0 && MODE != 1) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && MODE != 1) {
         scales[0] = s_n;
         scales[1] = s_g;
     }
     float mn = 0.0f, mg = 0.0f;
-    if (i < nx && j < ny) {
+    if (J < Hh) {
+        const int i = min(max(I - h, 0), nx - 1), j = min(max(J - h, 0), ny - 1);
         const size_t sy = nx, sz = static_cast<size_t>(nx) * ny;
         const float* col = rho + static_cast<size_t>(j) * sy + i;
         const bool xl = i > 0, xh = i < nx - 1, yl = j > 0, yh = j < ny - 1;
@@ -80,9 +90,15 @@ __global__ void __launch_bounds__(256) field_column_kernel(const float* __restri
             e.gx = !xl ? dxh - dcur : (!xh ? dcur - dxl : (dxh - dxl) * 0.5f);
             e.gy = !yl ? dyh - dcur : (!yh ? dcur - dyl : (dyh - dyl) * 0.5f);
             e.gz = (k == 0) ? dnext - dcur : (k == nz - 1 ? dcur - dprev : (dnext - dprev) * 0.5f);
+            const size_t o = h ? brick2_offset(I, J, k + 1, L.bx, L.bxy)
+                               : (static_cast<size_t>(k) * ny + j) * nx + i;
+            // z halo copies of the first and last slice
+            const bool zh = h && (k == 0 || k == nz - 1);
+            const size_t oh = zh ? brick2_offset(I, J, k == 0 ? 0 : nz + 1, L.bx, L.bxy) : 0;
             if (MODE == 0) {
-                static_cast<float4*>(out)[out_index(L, i, j, k, nx, ny)] =
-                    make_float4(e.dn, e.gx, e.gy, e.gz);
+                const float4 v = make_float4(e.dn, e.gx, e.gy, e.gz);
+                static_cast<float4*>(out)[o] = v;
+                if (zh) static_cast<float4*>(out)[oh] = v;
             } else if (MODE == 1) {
                 mn = fmaxf(mn, fabsf(e.dn));
                 mg = fmaxf(mg, fmaxf(fabsf(e.gx), fmaxf(fabsf(e.gy), fabsf(e.gz))));
@@ -92,7 +108,8 @@ __global__ void __launch_bounds__(256) field_column_kernel(const float* __restri
                 q.y = __half_as_ushort(__float2half_rn(e.gx / s_g));
                 q.z = __half_as_ushort(__float2half_rn(e.gy / s_g));
                 q.w = __half_as_ushort(__float2half_rn(e.gz / s_g));
-                static_cast<ushort4*>(out)[out_index(L, i, j, k, nx, ny)] = q;
+                static_cast<ushort4*>(out)[o] = q;
+                if (zh) static_cast<ushort4*>(out)[oh] = q;
             }
             dprev = dcur;
             dcur = dnext;
@@ -104,12 +121,12 @@ __global__ void __launch_bounds__(256) field_column_kernel(const float* __restri
             mg = fmaxf(mg, __shfl_xor_sync(0xffffffffu, mg, o));
         }
         __shared__ float sn[8], sg[8];
-        if (threadIdx.x == 0) {
-            sn[threadIdx.y] = mn;
-            sg[threadIdx.y] = mg;
+        if ((threadIdx.x & 31) == 0) {
+            sn[threadIdx.x >> 5] = mn;
+            sg[threadIdx.x >> 5] = mg;
         }
         __syncthreads();
-        if (threadIdx.y == 0 && threadIdx.x == 0) {
+        if (threadIdx.x == 0) {
             for (int w = 1; w < 8; ++w) {
                 mn = fmaxf(mn, sn[w]);
                 mg = fmaxf(mg, sg[w]);
@@ -145,8 +162,14 @@ __global__ void export_kernel(const void* __restrict__ data, int storage, OutLay
 
 cudaError_t launch_field(const float* rho, int nx, int ny, int nz, float K, hh_volume_s* vol,
                          cudaStream_t s) {
-    const dim3 block(32, 8);
-    const dim3 grid((nx + 31) / 32, (ny + 7) / 8, (nz + FIELD_ZRUN - 1) / FIELD_ZRUN);
+    // 256 threads per block over the stored (x, y) columns; blockIdx.y picks
+    // the z run. The FP16 max pass covers the grid columns only (no halo).
+    const int h2 = vol->layout == HH_LAYOUT_BRICK2 ? 2 : 0;
+    const dim3 block(256);
+    const dim3 grid(static_cast<unsigned>((static_cast<int64_t>(nx + h2) * (ny + h2) + 255) / 256),
+                    (nz + FIELD_ZRUN - 1) / FIELD_ZRUN);
+    const dim3 grid_max(static_cast<unsigned>((static_cast<int64_t>(nx) * ny + 255) / 256),
+                        (nz + FIELD_ZRUN - 1) / FIELD_ZRUN);
     const OutLayout L{vol->layout, vol->bx, vol->bxy};
     if (vol->storage == HH_STORE_FP32) {
         field_column_kernel<0><<<grid, block, 0, s>>>(rho, nx, ny, nz, K, L, vol->data, nullptr,
@@ -156,7 +179,7 @@ cudaError_t launch_field(const float* rho, int nx, int ny, int nz, float K, hh_v
     }
     cudaError_t e = cudaMemsetAsync(vol->max_dev, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    field_column_kernel<1><<<grid, block, 0, s>>>(rho, nx, ny, nz, K, L, nullptr, vol->max_dev,
+    field_column_kernel<1><<<grid_max, block, 0, s>>>(rho, nx, ny, nz, K, L, nullptr, vol->max_dev,
                                                   vol->scales_dev);
     field_column_kernel<2><<<grid, block, 0, s>>>(rho, nx, ny, nz, K, L, vol->data, vol->max_dev,
                                                   vol->scales_dev);

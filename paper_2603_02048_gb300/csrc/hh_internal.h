@@ -15,9 +15,13 @@
 
 // Volume layouts.
 //  LINEAR: x fastest, index (k*ny + j)*nx + i (the export / interchange layout).
-//  BRICK2: 2x2x2 micro-bricks. Brick (X,Y,Z) = (i>>1, j>>1, k>>1) in x-fastest
-//          order over ceil(n/2) bricks per axis; inside a brick the voxel sits
-//          at slot (i&1) | (j&1)<<1 | (k&1)<<2. One FP32 brick is one 128-byte
+//  BRICK2: 2x2x2 micro-bricks over the grid with a one-voxel halo: voxel
+//          (i,j,k) sits at padded coordinates (I,J,K) = (i+1, j+1, k+1), and
+//          the halo (I = 0 or n+1 on some axis) holds a copy of the nearest
+//          grid voxel, so a trilinear sample clamped to the edge needs no
+//          index clamps. Brick (I>>1, J>>1, K>>1) in x-fastest order over
+//          ceil((n+2)/2) bricks per axis; inside a brick the voxel sits at
+//          slot (I&1) | (J&1)<<1 | (K&1)<<2. One FP32 brick is one 128-byte
 //          line, and the eight corners of any trilinear cell occupy eight
 //          different slots, i.e. eight different 16-byte L1 bank groups, so a
 //          warp's corner loads spread over all banks whatever the view
@@ -25,6 +29,12 @@
 //          power-of-two grid into the same bank group).
 enum { HH_LAYOUT_LINEAR = 0, HH_LAYOUT_BRICK2 = 1 };
 
+// Bricks along an axis of n voxels in the BRICK2 layout (halo included).
+__host__ __device__ __forceinline__ unsigned brick2_count(int n) {
+    return static_cast<unsigned>((n + 3) / 2);
+}
+
+// Element of padded coordinates (I, J, K) in the BRICK2 layout.
 __host__ __device__ __forceinline__ unsigned brick2_offset(unsigned i, unsigned j, unsigned k,
                                                            unsigned bx, unsigned bxy) {
     return (((k >> 1) * bxy + (j >> 1) * bx + (i >> 1)) << 3) | ((k & 1u) << 2) |
@@ -38,7 +48,7 @@ struct hh_volume_s {
     unsigned bx, bxy;   // BRICK2: bricks along x, bricks per xy plane
     float h_kernel;
     void* data;         // float4 (FP32) or ushort4 of halves (FP16) per voxel
-    size_t bytes;       // bytes of data (BRICK2 pads every axis to even)
+    size_t bytes;       // bytes of data (BRICK2: halo of one voxel, axes padded to even)
     float* scales_dev;  // [2] = {s_n, s_g} on the device (1, 1 for FP32)
     unsigned* max_dev;  // [2] = bit patterns of max|dn|, max|g| (FP16 build)
     float* rho_dev;     // density scratch for particle builds (nullable)

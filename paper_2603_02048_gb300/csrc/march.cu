@@ -145,12 +145,21 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return r;
 }
 
-// Lattice cell and weight along one axis: u = p - 1/2 clamped to [0, n-1],
-// i0 = min(floor(u), n-2), f = u - i0. NaN positions clamp to 0.
+// Lattice cell and weight along one axis, in the halo coordinates of the
+// BRICK2 layout (the centre of grid voxel i at u = i + 1): u = p + 1/2,
+// i0 = floor(u), f = u - i0. A position p in [0, n] gives u in [0.5, n + 0.5],
+// so both corners i0, i0 + 1 lie in the padded axis [0, n + 1], and the halo
+// copies make this the sample with the lattice coordinate clamped to the
+// voxel centres. The Euler march samples only accepted positions, which lie
+// in the box (a NaN position gives i0 = 0); CLAMP first clamps u to
+// [0.5, n + 0.5] (NaN to 0.5) for RK4 stage points, which may lie outside.
+template <bool CLAMP>
 __device__ __forceinline__ void axis_cell(float p, int n, int& i0, float& f) {
-    const float u = fminf(fmaxf(p - 0.5f, 0.0f), static_cast<float>(n - 1));
-    i0 = min(static_cast<int>(floorf(u)), n - 2);
-    f = u - static_cast<float>(i0);
+    float u = p + 0.5f;
+    if (CLAMP) u = fminf(fmaxf(u, 0.5f), static_cast<float>(n) + 0.5f);
+    const float fl = floorf(u);
+    i0 = static_cast<int>(fl);
+    f = u - fl;
 }
 
 __device__ __forceinline__ float4 ld_fp32(const float4* __restrict__ v, unsigned i) {
@@ -166,13 +175,13 @@ __device__ __forceinline__ float4 ld_fp16(const ushort4* __restrict__ v, unsigne
 // Trilinear sample of {dn, g} at p (Sec. 3.3.1: n and grad n sampled with
 // trilinear interpolation); FP16 volumes are interpolated as stored and
 // scaled once afterwards.
-template <int STORAGE>
+template <int STORAGE, bool CLAMP>
 __device__ __forceinline__ Sample fetch(const VolArgs& A, float3 p) {
     int ix, iy, iz;
     float fx, fy, fz;
-    axis_cell(p.x, A.nx, ix, fx);
-    axis_cell(p.y, A.ny, iy, fy);
-    axis_cell(p.z, A.nz, iz, fz);
+    axis_cell<CLAMP>(p.x, A.nx, ix, fx);
+    axis_cell<CLAMP>(p.y, A.ny, iy, fy);
+    axis_cell<CLAMP>(p.z, A.nz, iz, fz);
     // BRICK2 element of corner (ix, iy, iz), then the steps to the other
     // corners: +1 in x stays in the brick (slot +1) when ix is even, else it
     // moves to the next brick (slot -1, brick +1: +7); likewise y (+2 or
@@ -417,10 +426,10 @@ __device__ __forceinline__ float exit_fraction(const VolArgs& A, float3 hi, floa
     return fmaxf(tau, 0.0f);
 }
 
-template <int STORAGE, bool ADAPTIVE>
+template <int STORAGE, bool CLAMP>
 __device__ __forceinline__ float3 perp_rate(const VolArgs& A, float3 p, float3 w, float& n,
                                             float& gperp_norm) {
-    const Sample s = fetch<STORAGE>(A, p);
+    const Sample s = fetch<STORAGE, CLAMP>(A, p);
     n = 1.0f + s.dn;
     const float3 g = make_float3(s.gx, s.gy, s.gz);
     const float3 gp = fma3(-dot(w, g), w, g);
@@ -462,7 +471,12 @@ __device__ __forceinline__ void ray_begin(const VolArgs& V, const ViewArgs& C, i
     if (slab(V, C.eye, R.wr, t_in)) {
         R.flags = HH_FLAG_HIT;
         // position = (hi - B) + lo with hi = position + B (see the header)
-        const float3 entry = fma3(fmaxf(t_in, 0.0f), R.wr, C.eye);
+        // entry point, clamped into the box (rounding may put it just outside; the
+        // march samples only positions in the box)
+        float3 entry = fma3(fmaxf(t_in, 0.0f), R.wr, C.eye);
+        entry.x = fminf(fmaxf(entry.x, 0.0f), static_cast<float>(V.nx));
+        entry.y = fminf(fmaxf(entry.y, 0.0f), static_cast<float>(V.ny));
+        entry.z = fminf(fmaxf(entry.z, 0.0f), static_cast<float>(V.nz));
         fast_two_sum(V.bias, entry.x, R.hi.x, R.lo.x);
         fast_two_sum(V.bias, entry.y, R.hi.y, R.lo.y);
         fast_two_sum(V.bias, entry.z, R.hi.z, R.lo.z);
@@ -484,21 +498,21 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     if (STEPPER == HH_STEP_RK4) {
         float n1, gpn, n2, n3, n4, unused;
         const float3 w1 = wr + d;
-        const float3 gp1 = perp_rate<STORAGE, ADAPTIVE>(V, C, w1, n1, gpn);
+        const float3 gp1 = perp_rate<STORAGE, true>(V, C, w1, n1, gpn);
         ds = step_length<ADAPTIVE>(V, n1, gpn);
         const float hds = 0.5f * ds;
         const float3 k1 = __fdividef(1.0f, n1) * gp1;
         const float3 d2 = fma3(hds, k1, d);
         const float3 w2 = wr + d2;
-        const float3 gp2 = perp_rate<STORAGE, ADAPTIVE>(V, fma3(hds, w1, C), w2, n2, unused);
+        const float3 gp2 = perp_rate<STORAGE, true>(V, fma3(hds, w1, C), w2, n2, unused);
         const float3 k2 = __fdividef(1.0f, n2) * gp2;
         const float3 d3 = fma3(hds, k2, d);
         const float3 w3 = wr + d3;
-        const float3 gp3 = perp_rate<STORAGE, ADAPTIVE>(V, fma3(hds, w2, C), w3, n3, unused);
+        const float3 gp3 = perp_rate<STORAGE, true>(V, fma3(hds, w2, C), w3, n3, unused);
         const float3 k3 = __fdividef(1.0f, n3) * gp3;
         const float3 d4 = fma3(ds, k3, d);
         const float3 w4 = wr + d4;
-        const float3 gp4 = perp_rate<STORAGE, ADAPTIVE>(V, fma3(ds, w3, C), w4, n4, unused);
+        const float3 gp4 = perp_rate<STORAGE, true>(V, fma3(ds, w3, C), w4, n4, unused);
         const float3 k4 = __fdividef(1.0f, n4) * gp4;
         const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
         dnew = renormalize(wr, fma3(ds * (1.0f / 6.0f), ksum, d));
@@ -507,7 +521,7 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     } else {
         float n, gpn;
         const float3 w = wr + d;
-        const float3 gp = perp_rate<STORAGE, ADAPTIVE>(V, C, w, n, gpn);
+        const float3 gp = perp_rate<STORAGE, false>(V, C, w, n, gpn);
         ds = step_length<ADAPTIVE>(V, n, gpn);
         dnew = renormalize(wr, fma3(__fdividef(ds, n), gp, d));
         inc = ds * (wr + dnew);
