@@ -269,16 +269,18 @@ __device__ __forceinline__ float step_length(const VolArgs& A, float n, float gp
 }
 
 // Eq. 16's normalize, in deflection form: returns d' with w_ref + d' the unit
-// vector along w_ref + d1 (taking |w_ref| = 1): w_ref + d' = (1 + r)(w_ref + d1)
-// with 1 + r = (1 + e)^(-1/2), e = |w_ref + d1|^2 - 1 = 2 w_ref.d1 + |d1|^2.
-// r is the Taylor polynomial -e/2 + 3e^2/8 - 5e^3/16 (error 35 e^4 / 128):
-// e is the squared turn of one step plus the previous rounding (below 1e-5
-// when Eq. 18 bounds the turn by theta_max <= 3e-3), and an error in r only
-// scales the length of w, never its direction, and is undone at the next step.
-__device__ __forceinline__ float3 renormalize(float3 wr, float3 d1) {
-    const float e = fmaf(2.0f, dot(wr, d1), dot(d1, d1));
+// vector along w1 = w_ref + d1: w_ref + d' = (1 + r) w1 with
+// 1 + r = (1 + e)^(-1/2), e = |w1|^2 - 1, r by its Taylor polynomial
+// -e/2 + 3e^2/8 - 5e^3/16 (error 35 e^4 / 128). e is the squared turn of one
+// step plus the previous rounding (below 1e-5 when Eq. 18 bounds the turn by
+// theta_max <= 3e-3; an e below FP32 resolution rounds to 0 and leaves w1 as
+// it is, as FP32 normalisation would); r only scales w1, never turns it, and
+// its error is undone at the next step. Only d is carried, so the rounding of
+// the update never touches the O(1) part w_ref.
+__device__ __forceinline__ float3 renormalize(float3 w1, float3 d1) {
+    const float e = fmaf(w1.x, w1.x, fmaf(w1.y, w1.y, fmaf(w1.z, w1.z, -1.0f)));
     const float rm1 = e * fmaf(e, fmaf(-0.3125f, e, 0.375f), -0.5f);
-    return fma3(rm1, wr + d1, d1);
+    return fma3(rm1, w1, d1);
 }
 
 // Colour of direction d in the equirect environment map (bilinear, u wraps,
@@ -494,7 +496,7 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     const float3 wr = R.wr, d = R.d;
     const float3 C = R.c;
     float ds;
-    float3 dnew, inc;
+    float3 dnew, wnew, inc;
     if (STEPPER == HH_STEP_RK4) {
         float n1, gpn, n2, n3, n4, unused;
         const float3 w1 = wr + d;
@@ -515,7 +517,9 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
         const float3 gp4 = perp_rate<STORAGE, true>(V, fma3(ds, w3, C), w4, n4, unused);
         const float3 k4 = __fdividef(1.0f, n4) * gp4;
         const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
-        dnew = renormalize(wr, fma3(ds * (1.0f / 6.0f), ksum, d));
+        const float3 dsum = fma3(ds * (1.0f / 6.0f), ksum, d);
+        dnew = renormalize(wr + dsum, dsum);
+        wnew = wr + dnew;
         const float3 dpos = (1.0f / 6.0f) * (d + 2.0f * (d2 + d3) + d4);
         inc = ds * (wr + dpos);
     } else {
@@ -523,8 +527,10 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
         const float3 w = wr + d;
         const float3 gp = perp_rate<STORAGE, false>(V, C, w, n, gpn);
         ds = step_length<ADAPTIVE>(V, n, gpn);
-        dnew = renormalize(wr, fma3(__fdividef(ds, n), gp, d));
-        inc = ds * (wr + dnew);
+        const float3 d1 = fma3(__fdividef(ds, n), gp, d);
+        dnew = renormalize(wr + d1, d1);
+        wnew = wr + dnew;
+        inc = ds * wnew;
     }
     float3 nhi, err;
     fast_two_sum(R.hi.x, inc.x, nhi.x, err.x);
@@ -537,7 +543,7 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
         const float3 h0 = make_float3(R.hi.x - B, R.hi.y - B, R.hi.z - B);  // exact
         const float tau = exit_fraction(V, h0, R.lo, inc);
         ep = h0 + fma3(tau, inc, R.lo);
-        ed = wr + dnew;
+        ed = wnew;
         R.flags |= HH_FLAG_EXITED;
         return true;
     }
