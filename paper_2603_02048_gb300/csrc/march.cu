@@ -43,6 +43,11 @@ constexpr float kPi = 3.14159265358979323846f;
 // Resident 128-thread blocks per SM the Eq. 16 march kernels are compiled
 // for: 8 leaves 64 registers per thread (measured fastest; 10 or 12 spill).
 #define HH_MARCH_MIN_BLOCKS 8
+// Resident 256-thread blocks per SM of the persistent batched kernel (its
+// refill state needs registers beyond the single-view kernel's).
+#ifndef HH_BATCH_MIN_BLOCKS
+#define HH_BATCH_MIN_BLOCKS 4
+#endif
 
 // Volume-side arguments of a launch (shared by every view).
 struct VolArgs {
@@ -614,9 +619,11 @@ __global__ void __launch_bounds__(128, (STEPPER == HH_STEP_RK4) ? 6 : HH_MARCH_M
 // ran out of steps), the idle lanes take the next pixels of the warp's
 // current tile (and of the next tile when it runs out) while the other lanes
 // keep marching; refill_min = 32 refills only when every lane is idle, i.e.
-// plain tile-at-a-time scheduling. The per-ray arithmetic is march_kernel's.
-template <int STORAGE, int STEPPER, bool ADAPTIVE>
-__global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_MARCH_MIN_BLOCKS / 2)
+// plain tile-at-a-time scheduling, compiled separately (REFILL = false) as
+// march_kernel's loop around a tile counter. The per-ray arithmetic is
+// march_kernel's.
+template <int STORAGE, int STEPPER, bool ADAPTIVE, bool REFILL>
+__global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_MIN_BLOCKS)
     march_batch_kernel(const VolArgs V, const ViewArgs* __restrict__ views, int n_views,
                        int total_tiles, int tile_w, unsigned* __restrict__ counter,
                        int refill_min) {
@@ -628,6 +635,35 @@ __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_MARCH_M
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int tile_w_log2 = tile_w == 16 ? 4 : (tile_w == 8 ? 3 : 2);
+    if (!REFILL) {
+        int lx, ly;
+        tile_pixel(lane, tile_w_log2, lx, ly);
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = static_cast<int>(atomicAdd(counter, 1u));
+            t = __shfl_sync(FULL, t, 0);
+            if (t >= total_tiles) return;
+            int lo = 0, hi = n_views - 1;  // last view whose first tile <= t
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_begin[mid] <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            const ViewArgs& C = views[lo];
+            const int local = t - s_begin[lo];
+            const int ty = local / C.tiles_x, tx = local - ty * C.tiles_x;
+            const int px = (tx << tile_w_log2) + lx, py = ty * (32 >> tile_w_log2) + ly;
+            if (px < C.W && py < C.H) {
+                RayState R;
+                float3 ep = make_float3(0.0f, 0.0f, 0.0f), ed = ep;
+                ray_begin(V, C, px, py, R);
+                if (R.flags & HH_FLAG_HIT)
+                    while (R.k < V.max_steps && !ray_step<STORAGE, STEPPER, ADAPTIVE>(V, R, ep, ed)) {
+                    }
+                ray_end(V, C, px, py, R, ep, ed);
+            }
+        }
+    }
     int tile = 0, tile_view = 0, pos = 32;  // the warp's pixel stream (warp-uniform)
     bool done = false, have = false;
     int vi = 0, px = 0, py = 0;
@@ -720,21 +756,31 @@ struct SingleLaunch {
     }
 };
 
+// refill_min >= 32 runs the tile-at-a-time instantiation (REFILL = false).
 template <int ST, int SP, bool AD>
 struct BatchLaunch {
     static void run(const VolArgs& V, const ViewArgs* views, int n_views, int total_tiles,
                     int tile_w, unsigned* counter, int refill_min, int blocks, int threads,
                     cudaStream_t s) {
-        march_batch_kernel<ST, SP, AD><<<blocks, threads, (n_views + 1) * sizeof(int), s>>>(
-            V, views, n_views, total_tiles, tile_w, counter, refill_min);
+        const size_t smem = (n_views + 1) * sizeof(int);
+        if (refill_min >= 32)
+            march_batch_kernel<ST, SP, AD, false><<<blocks, threads, smem, s>>>(
+                V, views, n_views, total_tiles, tile_w, counter, refill_min);
+        else
+            march_batch_kernel<ST, SP, AD, true><<<blocks, threads, smem, s>>>(
+                V, views, n_views, total_tiles, tile_w, counter, refill_min);
     }
 };
 
 template <int ST, int SP, bool AD>
 struct BatchOccupancy {
-    static void run(int threads, size_t smem, int* blocks_per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, march_batch_kernel<ST, SP, AD>,
-                                                      threads, smem);
+    static void run(int threads, size_t smem, int refill_min, int* blocks_per_sm) {
+        if (refill_min >= 32)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                blocks_per_sm, march_batch_kernel<ST, SP, AD, false>, threads, smem);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                blocks_per_sm, march_batch_kernel<ST, SP, AD, true>, threads, smem);
     }
 };
 
@@ -849,7 +895,7 @@ cudaError_t launch_batch(const hh_volume_s* vol, const hh_step_params& P, const 
     int bps = cfg.blocks_per_sm;
     if (bps <= 0) {
         dispatch<BatchOccupancy>(vol->storage, P.stepper, P.adaptive, cfg.block_threads,
-                                 (n_views + 1) * sizeof(int), &bps);
+                                 (n_views + 1) * sizeof(int), cfg.refill_min, &bps);
         bps = max(bps, 1);
     }
     const VolArgs V = make_vol_args(vol, P, bg);
@@ -927,17 +973,18 @@ hh_status check_config(const hh_batch_config* c) {
     return HH_OK;
 }
 
-int resident_blocks(hh_batch b, int threads) {
+int resident_blocks(hh_batch b, int threads, int refill_min) {
     int bps = 0;
     const size_t smem = (b->cams.size() + 1) * sizeof(int);
     hh::dispatch<hh::BatchOccupancy>(b->vol->storage, b->params.stepper, b->params.adaptive,
-                                     threads, smem, &bps);
+                                     threads, smem, refill_min, &bps);
     return std::max(bps, 1);
 }
 
 int grid_blocks(hh_batch b) {
-    const int bps = b->cfg.blocks_per_sm > 0 ? b->cfg.blocks_per_sm
-                                              : resident_blocks(b, b->cfg.block_threads);
+    const int bps = b->cfg.blocks_per_sm > 0
+                        ? b->cfg.blocks_per_sm
+                        : resident_blocks(b, b->cfg.block_threads, b->cfg.refill_min);
     return b->sm_count * bps;
 }
 
@@ -1027,7 +1074,8 @@ hh_status hh_batch_set_config(hh_batch b, const hh_batch_config* cfg) {
 hh_status hh_batch_get_config(hh_batch b, hh_batch_config* cfg) {
     if (!b || !cfg) return fail(HH_ERR_INVALID_ARG, "batch or config is NULL");
     *cfg = b->cfg;
-    if (cfg->blocks_per_sm == 0) cfg->blocks_per_sm = resident_blocks(b, b->cfg.block_threads);
+    if (cfg->blocks_per_sm == 0)
+        cfg->blocks_per_sm = resident_blocks(b, b->cfg.block_threads, b->cfg.refill_min);
     return hh::ok();
 }
 
@@ -1093,7 +1141,8 @@ hh_status hh_batch_autotune(hh_batch b, int reps, void* stream, hh_batch_config*
     hh_batch_config best_cfg = b->cfg;
     hh_status st = HH_OK;
     for (auto c : cand) {
-        if (c.blocks_per_sm < 0) c.blocks_per_sm = std::max(1, resident_blocks(b, c.block_threads) / 2);
+        if (c.blocks_per_sm < 0)
+            c.blocks_per_sm = std::max(1, resident_blocks(b, c.block_threads, c.refill_min) / 2);
         if ((st = hh_batch_set_config(b, &c)) != HH_OK) break;
         std::vector<float> t;
         const int blocks = grid_blocks(b);
