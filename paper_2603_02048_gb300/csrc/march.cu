@@ -46,7 +46,7 @@ constexpr float kPi = 3.14159265358979323846f;
 // Resident 256-thread blocks per SM of the persistent batched kernel (its
 // refill state needs registers beyond the single-view kernel's).
 #ifndef HH_BATCH_MIN_BLOCKS
-#define HH_BATCH_MIN_BLOCKS 4
+#define HH_BATCH_MIN_BLOCKS 3
 #endif
 
 // Volume-side arguments of a launch (shared by every view).
