@@ -107,6 +107,36 @@ def test_ragged_grid_and_views_in_one_call(gpu, oracle_lib, bg):
     assert stats[1]["hits"] == 33 * 17  # every ray starts inside
 
 
+@pytest.mark.parametrize("storage,stepper", [("fp32", "euler"), ("fp32", "rk4"), ("fp16", "euler")])
+def test_field_up_to_faces_edges_and_corners(gpu, oracle_lib, bg, storage, stepper):
+    """Turbulence of constant strength fills the whole box, faces included, on
+    a ragged grid: rays that enter through faces, edges and corners and graze
+    the faces sample within half a voxel of them, where the lattice
+    coordinate is clamped to the voxel centres (the stored halo), and must
+    agree with the oracle's clamped trilinear sample."""
+    hh, torch = gpu
+    dims = (37, 29, 23)
+    dn = hi.homogeneous_turbulence_dn(dims, seed=7, sigma=1.5, std=2e-5)
+    assert np.abs(dn[:, :, 0]).max() > 1e-5 and np.abs(dn[-1]).max() > 1e-5
+    vol = _dn_volume(hh, torch, dn, storage)
+    c = [18.5, 14.5, 11.5]
+    cams = [hi.orbit_camera(dims, 45.0, 35.3, 48, 40),  # towards a corner
+            hi.orbit_camera(dims, 0.0, 0.0, 61, 33, vfov_deg=50.0),
+            # grazing: eyes just outside faces, looking along them
+            {"eye": [-0.25, -5.0, 11.5], "look_at": [-0.25, 40.0, 11.0], "up": [0, 0, 1],
+             "vfov_deg": 20.0, "width": 24, "height": 24},
+            {"eye": [18.5, 14.5, 40.0], "look_at": [18.6, 14.4, 0.0], "up": [0, 1, 0],
+             "vfov_deg": 95.0, "width": 32, "height": 32},
+            {"eye": c, "look_at": [36.9, 28.9, 22.9], "up": [0, 0, 1],
+             "vfov_deg": 120.0, "width": 20, "height": 20}]  # from inside, out through every face
+    if stepper == "euler":
+        params = hi.params_euler_adaptive(dims, theta_max=1e-5, h_min=0.05, h_max=1.0)
+    else:
+        params = hi.params_rk4_fixed(dims, 0.35)
+    stats = _check(gpu, oracle_lib, vol, dims, cams, params, bg)
+    assert stats[0]["hits"] > 500 and stats[4]["hits"] == 400
+
+
 def test_max_steps_and_misses(gpu, oracle_lib, bg):
     """max_steps cuts rays inside the box (MAXSTEPS flag, exit at the current
     position); a camera looking away from the box sees the background along
