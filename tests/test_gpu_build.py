@@ -77,7 +77,7 @@ def _field_gpu(hh, torch, rho, K, storage):
     return out, info
 
 
-@pytest.mark.parametrize("dims", [(64, 64, 64), (33, 2, 17), (5, 40, 3)])
+@pytest.mark.parametrize("dims", [(64, 64, 64), (33, 2, 17), (5, 40, 3), (64, 7, 9), (32, 15, 70)])
 def test_field_fp32_matches_oracle(gpu, oracle_lib, dims):
     hh, torch = gpu
     rho = np.random.default_rng(1).uniform(0.0, 2.5, size=dims[::-1]).astype(np.float32)
@@ -149,3 +149,4 @@ def test_build_index_field_matches_parts(gpu, oracle_lib):
     m = np.abs(want[..., 0]).max()
     assert np.abs(got[..., 0] - want[..., 0]).max() <= 2e-5 * m
     assert np.abs(got[..., 1:] - want[..., 1:]).max() <= 2e-5 * m
+
