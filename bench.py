@@ -202,10 +202,45 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 # our arm
 # --------------------------------------------------------------------------- #
+def issue_rate(workload: str, ms_march: float, clocks: dict):
+    """What bounds the march in practice: warp instructions issued per second
+    (the committed ncu count per launch over the event-timed launch) against
+    the issue peak of 152 SMs x 4 schedulers x 1 warp-instruction per cycle at
+    the median SM clock sampled during the run; None without a count for the
+    current source."""
+    inst = march_counters(workload).get("warp_instructions_per_launch")
+    mhz = (clocks or {}).get("sm_mhz")
+    if not inst or not mhz or not ms_march:
+        return None
+    achieved = inst / (ms_march * 1e-3) / 1e9
+    peak = 152 * 4 * mhz * 1e6 / 1e9
+    return {"bound": "issue", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp-instructions/s", "frac": round(achieved / peak, 4),
+            "warp_instructions_per_launch": int(inst)}
+
+
+def march_counters(workload: str) -> dict:
+    """Counters of one march launch from the committed ncu capture (DRAM bytes,
+    warp instructions), or {} when the march source has changed since they
+    were taken."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "march_traffic.json")
+    src = os.path.join(ROOT, "paper_2603_02048_gb300", "csrc", "march.cu")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        rec = json.load(f)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if rec.get("march_cu_sha256") != sha:
+        return {}
+    return rec.get("workloads", {}).get(workload, {})
+
+
 def traffic_for(workload: str):
     """DRAM bytes per march launch from the committed ncu capture, or None
     when the march source has changed since the counters were taken."""
-    import hashlib
+    return march_counters(workload).get("dram_bytes_per_launch")
 
     path = os.path.join(ROOT, "profiles", "march_traffic.json")
     src = os.path.join(ROOT, "paper_2603_02048_gb300", "csrc", "march.cu")
@@ -407,6 +442,7 @@ def run_ours(args):
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic_for(args.workload), "kernel": kname,
                      "peak_kind": peak_kind, "algorithmic_bytes": int(march_bytes)},
+        "issue": issue_rate(args.workload, ms_march, clocks.summary()),
         "clocks": clocks.summary(),
         "cpu_baseline": cpu,
     }
