@@ -544,18 +544,19 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     const float3 nlo = R.lo + err;
     const float3 P = make_float3((nhi.x - B) + nlo.x, (nhi.y - B) + nlo.y, (nhi.z - B) + nlo.z);
     ++R.k;
-    if (outside(V, P)) {
-        const float3 h0 = make_float3(R.hi.x - B, R.hi.y - B, R.hi.z - B);  // exact
-        const float tau = exit_fraction(V, h0, R.lo, inc);
-        ep = h0 + fma3(tau, inc, R.lo);
-        ed = wnew;
-        R.flags |= HH_FLAG_EXITED;
-        return true;
-    }
+    const float3 ohi = R.hi, olo = R.lo;
     R.hi = nhi;
     R.lo = nlo;
     R.c = P;
     R.d = dnew;
+    if (outside(V, P)) {
+        const float3 h0 = make_float3(ohi.x - B, ohi.y - B, ohi.z - B);  // exact
+        const float tau = exit_fraction(V, h0, olo, inc);
+        ep = h0 + fma3(tau, inc, olo);
+        ed = wnew;
+        R.flags |= HH_FLAG_EXITED;
+        return true;
+    }
     return false;
 }
 
