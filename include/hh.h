@@ -7,7 +7,8 @@
  * refractive-index volume by Gladstone-Dale with its gradient by finite
  * differences (Eqs. 12-13), and one curved ray per pixel is integrated through
  * it (Eqs. 14-16) with the curvature-adaptive step of Eqs. 17-18; the exit ray
- * looks up a background (the stand-in for the paper's scene intersection).
+ * then sees the scene behind the volume: analytic textured planes and an
+ * environment map (the stand-in for the paper's scene intersection).
  *
  * Conventions shared by every call
  *  - Units are voxels. A grid of nx*ny*nz voxels covers the box
@@ -231,8 +232,10 @@ hh_status hh_volume_free(hh_volume vol);
  * sampled trilinearly at C_k (lattice coordinate p - 1/2 clamped to the
  * voxel centres), g_perp = (I - w w^T) g, ds by the schedule, then Eq. 16
  * (EULER_PAPER) or RK4; when a step leaves the box the segment is clipped
- * at the face and the ray leaves with the new direction. The colour is the
- * background at the exit direction. outs[i] belongs to cams[i]. */
+ * at the face and the ray leaves with the new direction. The colour is what
+ * the straight ray from the exit point along the exit direction sees in `bg`
+ * (its nearest textured plane, else the environment map); a ray that misses
+ * the box sees it along its primary ray. outs[i] belongs to cams[i]. */
 hh_status hh_trace(hh_volume vol, const hh_camera* cams, int n_cams,
                    const hh_step_params* params, const hh_background* bg,
                    const hh_view_out* outs, void* stream);

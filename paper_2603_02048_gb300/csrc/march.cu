@@ -1,16 +1,16 @@
 // Curved-ray march (Sec. 3.3.2-3.3.3 of arXiv 2603.02048), one thread per
 // pixel ray: pinhole ray generation, slab entry into the volume box, the
 // march of Eq. 15 with the Eq. 16 update (or RK4) and the Eq. 18 adaptive
-// step, the exit clip at the box face, and the bilinear equirect background
-// at the exit direction.
+// step, the exit clip at the box face, and what the straight exit ray sees
+// (textured scene planes, else the bilinear equirect environment map).
 //
 // Precision (everything FP32, no FP64 on the device):
 //  - The direction is carried as w = w_ref + d, with w_ref the primary ray
 //    direction (fixed per ray) and d the small accumulated deflection. The
-//    Eq. 16 normalisation is done in that form, d' = d1 + (r - 1)(w_ref + d1)
-//    with r - 1 = -e / (s (1 + s)), e = 2 w_ref.d1 + |d1|^2, s = sqrt(1 + e),
-//    so rounding never touches the O(1) part of w and the deflection keeps
-//    full relative precision over thousands of steps.
+//    Eq. 16 normalisation is done in that form, d' = d1 + r (w_ref + d1) with
+//    1 + r = |w_ref + d1|^-1 (a Taylor polynomial in e = |w_ref + d1|^2 - 1,
+//    see renormalize), so rounding never touches the O(1) part of w and the
+//    deflection keeps full relative precision over thousands of steps.
 //  - The position is a compensated pair (hi + lo): hi carries a power-of-two
 //    bias B (hi = position + B, B above every coordinate and step), so every
 //    increment is smaller than hi and Fast2Sum is error-free; its rounding
@@ -24,8 +24,9 @@
 // Layout: a block of 128 threads covers a 16x8 pixel tile; each warp an 8x4
 // sub-tile, so the rays of a warp stay close in the volume and their eight
 // corner fetches per step share cache lines in L1. The volume is stored in
-// 2x2x2 micro-bricks (BRICK2), which spreads the distinct voxels of a warp's
-// corner load over all L1 bank groups.
+// 2x2x2 micro-bricks (BRICK2) with a one-voxel halo of edge copies: the
+// bricks spread the distinct voxels of a warp's corner load over all L1 bank
+// groups, and the halo lets a sample in the box skip every index clamp.
 #include <algorithm>
 #include <cmath>
 #include <map>
