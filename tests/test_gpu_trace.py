@@ -186,3 +186,37 @@ def test_fp16_precision_against_fp64_truth(gpu, oracle_lib, bg):
         mse = np.mean((g["rgb"] - ref["rgb"]) ** 2)
         psnr = 10 * np.log10(1.0 / max(mse, 1e-30))
         assert psnr >= 50.0, psnr
+
+
+def test_gpu_adaptive_against_converged_truth(gpu, oracle_lib, bg):
+    """The GPU's adaptive march (FP32 and FP16 storage) against the converged
+    FP64 truth (RK4 of Eq. 15 at 1/64 voxel on the FP32 volume): the errors
+    the schedule and the storage leave, reported next to the oracle's own
+    adaptive march on the same rays (tests/test_oracle_method_accuracy.py)."""
+    hh, torch = gpu
+    dims = (64, 64, 64)
+    parts = hi.plume_particles(16384, 64)
+    v32 = _particle_volume(hh, torch, parts, dims, "fp32")
+    v16 = _particle_volume(hh, torch, parts, dims, "fp16")
+    cam = f32(hi.orbit_camera(dims, 0.0, 0.0, 128, 128))
+    pix = np.arange(0, 128 * 128, 41)
+    vol4 = export_volume(hh, torch, v32, dims)
+    truth = oracle_lib.trace_grid(vol4, cam, f32(hi.params_rk4_fixed(dims, 1.0 / 64.0)), bg[0],
+                                  pixels=pix, nthreads=NTHREADS)
+    params = f32(hi.params_euler_adaptive(dims, theta_max=hi.THETA_CALIBRATED))
+    own = oracle_lib.trace_grid(vol4, cam, params, bg[0], pixels=pix, nthreads=NTHREADS)
+    hit = (truth["flags"] & 1) != 0
+    from parity_util import angle
+
+    err = {"oracle": angle(own["exit_dir"][hit], truth["exit_dir"][hit])}
+    for name, v in (("gpu_fp32", v32), ("gpu_fp16", v16)):
+        g = gpu_trace(hh, torch, v, [cam], params, bg[1])[0]
+        err[name] = angle(g["exit_dir"][pix][hit], truth["exit_dir"][hit])
+    for k, a in err.items():
+        print(f"{k:9s} exit direction vs truth: median {np.median(a):.2e} "
+              f"p99 {np.quantile(a, 0.99):.2e} max {a.max():.2e} rad")
+    for k in ("gpu_fp32", "gpu_fp16"):
+        assert np.median(err[k]) <= 2 * np.median(err["oracle"]) + 1e-7, k
+        assert np.quantile(err[k], 0.99) <= 5e-5 and err[k].max() <= 1e-4, k
+    v32.close()
+    v16.close()
