@@ -135,17 +135,19 @@ typedef struct {
     hh_plane planes[HH_MAX_PLANES];
 } hh_background;
 
-/* Per-view outputs (device, caller-owned), pixel-major in row order. rgb is
- * required (H*W*3 floats in [0,1]); the others may be NULL.
- * exit_pos / exit_dir: H*W*3 floats (voxel units; a ray that misses the box
- * reports the eye and its primary direction); steps: H*W int32; flags:
- * H*W uint32 of HH_FLAG_* bits. */
+/* Per-view outputs (device, caller-owned), pixel-major in row order. At
+ * least one of rgb (H*W*3 floats in [0,1]) and rgb8 (H*W*3 bytes, the
+ * display image: round-to-nearest-even of 255 * rgb) is required; the
+ * others may be NULL. exit_pos / exit_dir: H*W*3 floats (voxel units; a ray
+ * that misses the box reports the eye and its primary direction); steps:
+ * H*W int32; flags: H*W uint32 of HH_FLAG_* bits. */
 typedef struct {
     float* rgb;
     float* exit_pos;
     float* exit_dir;
     int32_t* steps;
     uint32_t* flags;
+    uint8_t* rgb8;
 } hh_view_out;
 
 /* ---------------------------------------------------------------------- */
@@ -317,6 +319,7 @@ typedef struct hh_server_s* hh_server;
 #define HH_OUT_RGB 1   /* H*W*3 floats per view                         */
 #define HH_OUT_EXIT 2  /* exit_pos and exit_dir, H*W*3 floats each      */
 #define HH_OUT_STEPS 4 /* steps (int32) and flags (uint32), H*W each    */
+#define HH_OUT_RGB8 8  /* H*W*3 bytes per view (the display image)       */
 
 typedef struct {
     uint64_t submitted, admitted, completed, cancelled, failed, rejected;
@@ -341,7 +344,8 @@ hh_status hh_serve_put_volume(hh_server s, int64_t frame_id, hh_volume vol);
 hh_status hh_serve_remove_volume(hh_server s, int64_t frame_id);
 
 /* Queues a request of n_views cameras on frame `frame_id`; returns its
- * ticket at once. `outputs` is a mask of HH_OUT_* bits. */
+ * ticket at once. `outputs` is a mask of HH_OUT_* bits; without HH_OUT_RGB
+ * and HH_OUT_RGB8 the float image (HH_OUT_RGB) is made. */
 hh_status hh_serve_submit(hh_server s, int64_t frame_id, const hh_camera* cams, int n_views,
                           const hh_step_params* params, const hh_background* bg, int outputs,
                           uint64_t* ticket);

@@ -324,7 +324,8 @@ hh_status hh_trace(hh_volume vol, const hh_camera* cams, int n_cams,
     if ((st = check_background(bg)) != HH_OK) return st;
     for (int i = 0; i < n_cams; ++i) {
         if ((st = check_camera(cams[i], i)) != HH_OK) return st;
-        if (!outs[i].rgb) return fail(HH_ERR_INVALID_ARG, "view %d: rgb output is NULL", i);
+        if (!outs[i].rgb && !outs[i].rgb8)
+            return fail(HH_ERR_INVALID_ARG, "view %d: rgb and rgb8 outputs are both NULL", i);
     }
     for (int i = 0; i < n_cams; ++i) {
         cudaError_t e = launch_trace(vol, cams[i], *params, *bg, outs[i], as_stream(stream));

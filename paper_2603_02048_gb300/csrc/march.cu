@@ -74,6 +74,7 @@ struct ViewArgs {
     float a0, b0, s;   // pixel (x, y) -> a = a0 + (x + 1/2) s, b = b0 - (y + 1/2) s
     int W, H;
     float* rgb;
+    uint8_t* rgb8;
     float* exit_pos;
     float* exit_dir;
     int32_t* steps;
@@ -561,6 +562,11 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     return false;
 }
 
+// Display byte of a colour in [0, 1]: round-to-nearest-even of 255 v.
+__device__ __forceinline__ uint8_t to_u8(float v) {
+    return static_cast<uint8_t>(__float2uint_rn(__fmul_rn(fminf(fmaxf(v, 0.0f), 1.0f), 255.0f)));
+}
+
 // Final state, background lookup and the writes of one pixel. A ray that
 // missed reports the eye and its primary direction; one that ran out of
 // steps reports its current state (MAXSTEPS).
@@ -577,9 +583,16 @@ __device__ __forceinline__ void ray_end(const VolArgs& V, const ViewArgs& C, int
     }
     const float3 rgb = scene_color(V, ep, ed);
     const size_t pix = static_cast<size_t>(py) * C.W + px;
-    C.rgb[3 * pix + 0] = rgb.x;
-    C.rgb[3 * pix + 1] = rgb.y;
-    C.rgb[3 * pix + 2] = rgb.z;
+    if (C.rgb) {
+        C.rgb[3 * pix + 0] = rgb.x;
+        C.rgb[3 * pix + 1] = rgb.y;
+        C.rgb[3 * pix + 2] = rgb.z;
+    }
+    if (C.rgb8) {
+        C.rgb8[3 * pix + 0] = to_u8(rgb.x);
+        C.rgb8[3 * pix + 1] = to_u8(rgb.y);
+        C.rgb8[3 * pix + 2] = to_u8(rgb.z);
+    }
     if (C.exit_pos) {
         C.exit_pos[3 * pix + 0] = ep.x;
         C.exit_pos[3 * pix + 1] = ep.y;
@@ -848,6 +861,7 @@ ViewArgs make_view_args(const hh_camera& cam, const hh_view_out& out, int tile_w
     C.W = cam.width;
     C.H = cam.height;
     C.rgb = out.rgb;
+    C.rgb8 = out.rgb8;
     C.exit_pos = out.exit_pos;
     C.exit_dir = out.exit_dir;
     C.steps = out.steps;
@@ -1034,7 +1048,8 @@ hh_status hh_batch_create(hh_volume vol, const hh_camera* cams, int n_cams,
     if ((st = hh::check_background(bg)) != HH_OK) return st;
     for (int i = 0; i < n_cams; ++i) {
         if ((st = hh::check_camera(cams[i], i)) != HH_OK) return st;
-        if (!outs[i].rgb) return fail(HH_ERR_INVALID_ARG, "view %d: rgb output is NULL", i);
+        if (!outs[i].rgb && !outs[i].rgb8)
+            return fail(HH_ERR_INVALID_ARG, "view %d: rgb and rgb8 outputs are both NULL", i);
     }
     hh_batch b = new (std::nothrow) hh_batch_s();
     if (!b) return fail(HH_ERR_OOM, "host allocation failed");

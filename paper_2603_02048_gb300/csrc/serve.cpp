@@ -64,7 +64,9 @@ struct Slot {
 // Output bytes of one view for the requested outputs.
 size_t view_bytes(const hh_camera& c, int outputs) {
     const size_t px = static_cast<size_t>(c.width) * c.height;
-    size_t b = align256(px * 12);
+    size_t b = 0;
+    if (outputs & HH_OUT_RGB) b += align256(px * 12);
+    if (outputs & HH_OUT_RGB8) b += align256(px * 3);
     if (outputs & HH_OUT_EXIT) b += 2 * align256(px * 12);
     if (outputs & HH_OUT_STEPS) b += 2 * align256(px * 4);
     return b;
@@ -107,8 +109,14 @@ hh_status hh_server_s::launch(Request& r, int si) {
         const size_t px = static_cast<size_t>(r.cams[v].width) * r.cams[v].height;
         hh_view_out& o = r.outs[v];
         o = hh_view_out{};
-        o.rgb = reinterpret_cast<float*>(p);
-        p += align256(px * 12);
+        if (r.outputs & HH_OUT_RGB) {
+            o.rgb = reinterpret_cast<float*>(p);
+            p += align256(px * 12);
+        }
+        if (r.outputs & HH_OUT_RGB8) {
+            o.rgb8 = reinterpret_cast<uint8_t*>(p);
+            p += align256(px * 3);
+        }
         if (r.outputs & HH_OUT_EXIT) {
             o.exit_pos = reinterpret_cast<float*>(p);
             p += align256(px * 12);
@@ -312,8 +320,9 @@ hh_status hh_serve_submit(hh_server S, int64_t frame_id, const hh_camera* cams, 
     if (!S || !ticket) return hh::fail(HH_ERR_INVALID_ARG, "server or ticket is NULL");
     if (n_views < 1 || n_views > kMaxViews || !cams)
         return hh::fail(HH_ERR_INVALID_ARG, "a request has 1 to %d views", kMaxViews);
-    if (outputs & ~(HH_OUT_RGB | HH_OUT_EXIT | HH_OUT_STEPS))
+    if (outputs & ~(HH_OUT_RGB | HH_OUT_EXIT | HH_OUT_STEPS | HH_OUT_RGB8))
         return hh::fail(HH_ERR_INVALID_ARG, "unknown output bits");
+    if (!(outputs & (HH_OUT_RGB | HH_OUT_RGB8))) outputs |= HH_OUT_RGB;  // an image is always made
     hh_status st = hh::check_params(params);
     if (st != HH_OK) return st;
     if ((st = hh::check_background(bg)) != HH_OK) return st;
@@ -333,7 +342,7 @@ hh_status hh_serve_submit(hh_server S, int64_t frame_id, const hh_camera* cams, 
     r.cams.assign(cams, cams + n_views);
     r.params = *params;
     r.bg = *bg;
-    r.outputs = outputs | HH_OUT_RGB;
+    r.outputs = outputs;
     r.t_submit = now_ms();
     *ticket = r.ticket;
     S->pending.push_back(r.ticket);

@@ -76,7 +76,7 @@ class hh_background(ctypes.Structure):
 class hh_view_out(ctypes.Structure):
     _fields_ = [("rgb", ctypes.c_void_p), ("exit_pos", ctypes.c_void_p),
                 ("exit_dir", ctypes.c_void_p), ("steps", ctypes.c_void_p),
-                ("flags", ctypes.c_void_p)]
+                ("flags", ctypes.c_void_p), ("rgb8", ctypes.c_void_p)]
 
 
 class hh_batch_config(ctypes.Structure):
@@ -96,6 +96,7 @@ class hh_serve_stats(ctypes.Structure):
 HH_OUT_RGB = 1
 HH_OUT_EXIT = 2
 HH_OUT_STEPS = 4
+HH_OUT_RGB8 = 8
 
 
 # Every symbol include/hh.h declares, with (restype, argtypes).
@@ -342,8 +343,7 @@ def hh_trace(vol: Volume, cams, params, bg, outs, stream=None):
     c_cams = (hh_camera * max(n, 1))(*[c if isinstance(c, hh_camera) else make_camera(c)
                                        for c in cams])
     c_outs = (hh_view_out * max(n, 1))(*[
-        hh_view_out(_ptr(o["rgb"]), _ptr(o.get("exit_pos")), _ptr(o.get("exit_dir")),
-                    _ptr(o.get("steps")), _ptr(o.get("flags"))) for o in outs])
+        _view_out(o) for o in outs])
     P = params if isinstance(params, hh_step_params) else make_params(params)
     B = _background(bg)
     _check(load().hh_trace(vol.handle, c_cams, n, ctypes.byref(P), ctypes.byref(B), c_outs,
@@ -375,9 +375,15 @@ def _views(cams, outs):
     c_cams = (hh_camera * max(n, 1))(*[c if isinstance(c, hh_camera) else make_camera(c)
                                        for c in cams])
     c_outs = (hh_view_out * max(n, 1))(*[
-        hh_view_out(_ptr(o["rgb"]), _ptr(o.get("exit_pos")), _ptr(o.get("exit_dir")),
-                    _ptr(o.get("steps")), _ptr(o.get("flags"))) for o in outs])
+        _view_out(o) for o in outs])
     return n, c_cams, c_outs
+
+
+def _view_out(o: dict) -> hh_view_out:
+    """hh_view_out of a dict of CUDA tensors: rgb (float32) and/or rgb8
+    (uint8), and optional exit_pos, exit_dir, steps, flags."""
+    return hh_view_out(_ptr(o.get("rgb")), _ptr(o.get("exit_pos")), _ptr(o.get("exit_dir")),
+                       _ptr(o.get("steps")), _ptr(o.get("flags")), _ptr(o.get("rgb8")))
 
 
 def hh_batch_create(vol: Volume, cams, params, bg, outs) -> Batch:
@@ -505,7 +511,7 @@ def hh_serve_view(s: Server, ticket: int, view: int, width: int, height: int) ->
     out = {}
     for name, n, ts in (("rgb", npx * 3, "<f4"), ("exit_pos", npx * 3, "<f4"),
                         ("exit_dir", npx * 3, "<f4"), ("steps", npx, "<i4"),
-                        ("flags", npx, "<i4")):
+                        ("flags", npx, "<i4"), ("rgb8", npx * 3, "|u1")):
         ptr = getattr(o, name)
         if ptr:
             out[name] = torch.as_tensor(_DeviceArray(ptr, (n,), ts), device="cuda").clone()

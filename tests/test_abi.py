@@ -49,7 +49,7 @@ def test_struct_layouts_match_header(lib):
                                   "eps", "max_steps"],
                "hh_background": ["rgb8_dev", "width", "height", "n_planes", "planes"],
                "hh_plane": ["origin", "u", "v", "rgb8_dev", "width", "height"],
-               "hh_view_out": ["rgb", "exit_pos", "exit_dir", "steps", "flags"],
+               "hh_view_out": ["rgb", "exit_pos", "exit_dir", "steps", "flags", "rgb8"],
                "hh_batch_config": ["block_threads", "blocks_per_sm", "refill_min", "tile_w"],
                "hh_serve_stats": ["submitted", "admitted", "completed", "cancelled", "failed",
                                   "rejected", "pending", "running", "rays_completed",
