@@ -86,8 +86,9 @@ SERVE = {
     "text": ("60 device-resident 384^3 FP16 volumes of a drifting 1,048,576-particle plume "
              "(one per sim frame, 30 Hz); Poisson arrivals over 2 s, each request 1-16 views "
              "(uniform) at resolutions from {320x240, 1280x720, 1920x1080, 3840x2160}, eyes "
-             "1.5 grid widths away; continuous batching over 8 slot streams, 16 GiB output "
-             "budget; Eq. 16 adaptive, theta_max=3e-5")}
+             "1.5 grid widths away; each returns its rgb8 display images; continuous "
+             "batching over 8 slot streams, 16 GiB output budget; Eq. 16 adaptive, "
+             "theta_max=3e-5")}
 
 
 def scene(wl: dict):
@@ -523,7 +524,7 @@ def run_serve(args):
 
     # warm-up: a few requests through the whole path
     for req in hi.serving_requests(rate_hz=50, duration_s=0.2, n_frames=nf, seed=99)[:4]:
-        t = hh.hh_serve_submit(srv, req["frame"], cams_of(req), params, bg_t)
+        t = hh.hh_serve_submit(srv, req["frame"], cams_of(req), params, bg_t, hh.HH_OUT_RGB8)
         hh.hh_serve_wait(srv, t, 60000)
         hh.hh_serve_release(srv, t)
 
@@ -561,7 +562,7 @@ def run_serve(args):
             delay = start + t_arr - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            tk = hh.hh_serve_submit(srv, frame, cams, params, bg_t)
+            tk = hh.hh_serve_submit(srv, frame, cams, params, bg_t, hh.HH_OUT_RGB8)
             with lock:
                 tickets.append((tk, sum(c["width"] * c["height"] for c in cams)))
         th.join()
