@@ -430,7 +430,8 @@ class Server:
 
     def __init__(self, handle: ctypes.c_void_p):
         self.handle = handle
-        self._keep = []  # volumes and backgrounds the server borrows
+        self._frames = {}  # frame id -> the volume the server borrows
+        self._bgs = {}     # ticket -> the background its request reads
 
     def close(self):
         if self.handle is not None and self.handle.value:
@@ -458,11 +459,12 @@ def hh_serve_set_config(s: Server, block_threads=128, blocks_per_sm=0, refill_mi
 
 def hh_serve_put_volume(s: Server, frame_id: int, vol: Volume):
     _check(load().hh_serve_put_volume(s.handle, int(frame_id), vol.handle))
-    s._keep.append(vol)
+    s._frames[int(frame_id)] = vol
 
 
 def hh_serve_remove_volume(s: Server, frame_id: int):
     _check(load().hh_serve_remove_volume(s.handle, int(frame_id)))
+    s._frames.pop(int(frame_id), None)
 
 
 def hh_serve_submit(s: Server, frame_id: int, cams, params, bg, outputs: int = HH_OUT_RGB) -> int:
@@ -474,7 +476,7 @@ def hh_serve_submit(s: Server, frame_id: int, cams, params, bg, outputs: int = H
     t = ctypes.c_uint64()
     _check(load().hh_serve_submit(s.handle, int(frame_id), c_cams, n, ctypes.byref(P),
                                   ctypes.byref(B), int(outputs), ctypes.byref(t)))
-    s._keep.append(bg)
+    s._bgs[int(t.value)] = bg
     return int(t.value)
 
 
@@ -520,6 +522,7 @@ def hh_serve_view(s: Server, ticket: int, view: int, width: int, height: int) ->
 
 def hh_serve_release(s: Server, ticket: int):
     _check(load().hh_serve_release(s.handle, ctypes.c_uint64(ticket)))
+    s._bgs.pop(int(ticket), None)
 
 
 def hh_serve_cancel(s: Server, ticket: int):
