@@ -220,3 +220,32 @@ def test_gpu_adaptive_against_converged_truth(gpu, oracle_lib, bg):
         assert np.quantile(err[k], 0.99) <= 5e-5 and err[k].max() <= 1e-4, k
     v32.close()
     v16.close()
+
+
+def test_degenerate_grids_steps_and_eyes(gpu, oracle_lib, bg):
+    """Edge cases against the oracle: the smallest grid (2^3), a step longer
+    than the box (one step crosses it; RK4 stage points far outside), a single
+    step per ray, and eyes on a face and at a corner of the box."""
+    hh, torch = gpu
+    g = np.random.default_rng(21)
+    small = (2, 2, 2)
+    vol2 = _dn_volume(hh, torch, g.uniform(-1e-3, 1e-3, size=(2, 2, 2)).astype(np.float32))
+    cams2 = [hi.orbit_camera(small, 30.0, 20.0, 24, 16), hi.orbit_camera(small, 200.0, -45.0, 9, 9)]
+    for params in (hi.params_rk4_fixed(small, 0.25),
+                   hi.params_euler_adaptive(small, theta_max=1e-3, h_min=0.05, h_max=0.5)):
+        _check(gpu, oracle_lib, vol2, small, cams2, params, bg)
+    vol2.close()
+    dims = (24, 20, 16)
+    vol = _dn_volume(hh, torch, hi.homogeneous_turbulence_dn(dims, seed=3, sigma=1.5, std=3e-5))
+    cams = [hi.orbit_camera(dims, 10.0, 5.0, 32, 24),
+            {"eye": [0.0, 10.0, 8.0], "look_at": [24.0, 10.0, 8.0], "up": [0, 0, 1],  # on a face
+             "vfov_deg": 80.0, "width": 17, "height": 13},
+            {"eye": [24.0, 20.0, 16.0], "look_at": [0.0, 0.0, 0.0], "up": [0, 0, 1],  # at a corner
+             "vfov_deg": 60.0, "width": 15, "height": 15}]
+    for params in (dict(hi.params_rk4_fixed(dims, 50.0)),
+                   dict(hi.params_rk4_fixed(dims, 50.0), stepper="euler"),
+                   dict(hi.params_rk4_fixed(dims, 0.5), max_steps=1),
+                   dict(hi.params_euler_adaptive(dims, theta_max=1e-5), max_steps=1)):
+        st = _check(gpu, oracle_lib, vol, dims, cams, params, bg)
+        assert st[1]["hits"] > 0 and st[2]["hits"] > 0
+    vol.close()
