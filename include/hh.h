@@ -222,6 +222,10 @@ hh_status hh_volume_export(hh_volume vol, float* dst_dev, void* stream);
 hh_status hh_volume_info(hh_volume vol, hh_grid* grid, float* s_n, float* s_g, size_t* bytes,
                          void* stream);
 
+/* The FP16 scales alone (1, 1 for FP32 storage): hh_volume_info on the
+ * legacy default stream. Synchronises it; either output may be NULL. */
+hh_status hh_volume_scales(hh_volume vol, float* s_n, float* s_g);
+
 /* Releases the volume (cudaFree; synchronises the device first). NULL is ok. */
 hh_status hh_volume_free(hh_volume vol);
 

@@ -305,6 +305,10 @@ hh_status hh_volume_info(hh_volume vol, hh_grid* grid, float* s_n, float* s_g, s
     return ok();
 }
 
+hh_status hh_volume_scales(hh_volume vol, float* s_n, float* s_g) {
+    return hh_volume_info(vol, nullptr, s_n, s_g, nullptr, nullptr);
+}
+
 hh_status hh_volume_free(hh_volume vol) {
     if (!vol) return ok();
     cudaError_t e = cudaDeviceSynchronize();

@@ -119,6 +119,8 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_size_t), _P]),
+    "hh_volume_scales": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_float)]),
     "hh_volume_free": (ctypes.c_int, [_P]),
     "hh_trace": (ctypes.c_int, [_P, ctypes.POINTER(hh_camera), ctypes.c_int,
                                 ctypes.POINTER(hh_step_params), ctypes.POINTER(hh_background),
@@ -317,6 +319,13 @@ def hh_build_index_field_noalloc(xyzm, grid: hh_grid, K_gd: float, vol4, stream=
 
 def hh_volume_export(vol: Volume, dst, stream=None):
     _check(load().hh_volume_export(vol.handle, _ptr(dst), _stream(stream)))
+
+
+def hh_volume_scales(vol: Volume):
+    """(s_n, s_g) of the volume (1, 1 for FP32 storage)."""
+    s_n, s_g = ctypes.c_float(), ctypes.c_float()
+    _check(load().hh_volume_scales(vol.handle, ctypes.byref(s_n), ctypes.byref(s_g)))
+    return s_n.value, s_g.value
 
 
 def hh_volume_info(vol: Volume, stream=None) -> dict:

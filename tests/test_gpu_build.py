@@ -73,6 +73,7 @@ def _field_gpu(hh, torch, rho, K, storage):
 
     out = export_volume(hh, torch, vol, (nx, ny, nz))
     info = hh.hh_volume_info(vol)
+    info["scales"] = hh.hh_volume_scales(vol)
     vol.close()
     return out, info
 
@@ -88,7 +89,7 @@ def test_field_fp32_matches_oracle(gpu, oracle_lib, dims):
     # dn = fl(K rho): one rounding; g = fl(fl(dn1 - dn0) / 2): at most 3 roundings of max|dn|
     assert np.abs(got[..., 0] - want[..., 0]).max() <= 2.0**-24 * m * 1.01
     assert np.abs(got[..., 1:] - want[..., 1:]).max() <= 3 * 2.0**-24 * m * 1.01
-    assert info["s_n"] == 1.0 and info["s_g"] == 1.0
+    assert info["s_n"] == 1.0 and info["s_g"] == 1.0 and info["scales"] == (1.0, 1.0)
     # 2x2x2 micro-bricks over the grid and its one-voxel halo, every axis padded to even
     padded = 8 * ((dims[0] + 3) // 2) * ((dims[1] + 3) // 2) * ((dims[2] + 3) // 2)
     assert info["bytes"] == 16 * padded
@@ -123,6 +124,7 @@ def test_field_fp16_quantisation(gpu, oracle_lib):
     s_g = np.abs(want[..., 1:]).max() / 16384
     assert info["s_n"] == pytest.approx(s_n, rel=1e-6)
     assert info["s_g"] == pytest.approx(s_g, rel=1e-6)
+    assert info["scales"] == (info["s_n"], info["s_g"])
     assert info["bytes"] == 8 * 8 * 25**3  # 48 voxels + halo = 50 = 25 bricks per axis
     m = np.abs(want[..., 0]).max()
     for c, s in ((0, s_n), (1, s_g), (2, s_g), (3, s_g)):
