@@ -209,6 +209,14 @@ class ClockSampler:
 # --------------------------------------------------------------------------- #
 # our arm
 # --------------------------------------------------------------------------- #
+# FP32 operations of one Eq. 16 adaptive step as written in the march kernel
+# (an FMA counts 2): lattice coordinates 6, trilinear weights 15, the 8-corner
+# accumulation 60, n 1, w 3, g_perp and its norm 17, Eq. 18 step 4, ds/n 2,
+# Eq. 16 update 6, renormalisation 20, position increment 6, compensated
+# position 18.
+FLOPS_PER_STEP = 158
+
+
 def issue_rate(workload: str, ms_march: float, clocks: dict):
     """What bounds the march in practice: warp instructions issued per second
     (the committed ncu count per launch over the event-timed launch) against
@@ -425,6 +433,12 @@ def run_ours(args):
     per_step = 128 if wl["storage"] == "fp32" else 64
     march_bytes = total_steps * per_step + n_rays * 24
     achieved = march_bytes / (ms_march * 1e-3) / 1e9
+    # the other roofline leg: FP32 work at the FMA peak (152 SMs x 128 lanes x
+    # 2 flops per FMA at the sampled clock); FLOPS_PER_STEP is the per-op tally
+    # of one Eq. 16 adaptive step of the kernel source (an FMA counts 2)
+    fma_peak = 152 * 128 * 2 * (clocks.summary().get("sm_mhz") or 2070.0) * 1e6
+    legs_ms = {"hbm_counted_bytes": round(march_bytes / (peak * 1e9) * 1e3, 4),
+               "fp32_fma": round(total_steps * FLOPS_PER_STEP / fma_peak * 1e3, 4)}
     kname = ("march_kernel" if wl["mode"] == "trace" else "march_batch_kernel") + \
         f"<{wl['storage'].upper()}, EULER_PAPER, adaptive>"
     cpu = None
@@ -461,7 +475,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic_for(args.workload), "kernel": kname,
-                     "peak_kind": peak_kind, "algorithmic_bytes": int(march_bytes)},
+                     "peak_kind": peak_kind, "algorithmic_bytes": int(march_bytes),
+                     "leg_times_ms": legs_ms,
+                     "counters": {k: v for k, v in march_counters(args.workload).items()
+                                  if k in ("l1_hit_rate", "l2_hit_rate", "fma_pipe_pct",
+                                           "active_lanes_per_instruction")} or None},
         "issue": issue_rate(args.workload, ms_march, clk),
         "clocks": clk,
         "cpu_baseline": cpu,
