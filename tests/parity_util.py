@@ -154,6 +154,17 @@ def perturbation_spread(oracle, field, box, C0, w0, params, n_pert=6, seed=0, nt
     return s_dir, s_pos, s_steps
 
 
+def ill_conditioned(oracle, field, box, cam, params, pix):
+    """Which of the pixels pix (rays that hit) the oracle alone finds ill
+    conditioned: its exit direction or position moves by more than half a
+    tolerance, or its step count changes, under start-state perturbations at
+    FP32 rounding scale. Also returns the spreads."""
+    C0, w0 = start_states(oracle, cam, box, pix)
+    s_dir, s_pos, s_steps = perturbation_spread(oracle, field, box, C0, w0, params)
+    ill = (s_dir > DIR_TOL / 2) | (s_pos > POS_TOL / 2) | s_steps
+    return ill, s_dir, s_pos, s_steps
+
+
 def one_step_turn(params: dict, field) -> float:
     """Largest turning angle of one step: a step of length h turns by at most
     h max|grad n| / min n; Eq. 18 keeps unclamped and h_max-clamped steps
@@ -185,9 +196,7 @@ def assert_parity_conditioned(gpu: dict, ref: dict, oracle, field, box, cam, par
     st["n_bad"] = int(len(idx))
     st["n_ill"] = 0
     if len(idx):
-        C0, w0 = start_states(oracle, cam, box, pix[idx])
-        s_dir, s_pos, s_steps = perturbation_spread(oracle, field, box, C0, w0, params)
-        ill = (s_dir > DIR_TOL / 2) | (s_pos > POS_TOL / 2) | s_steps
+        ill, s_dir, s_pos, s_steps = ill_conditioned(oracle, field, box, cam, params, pix[idx])
         st["n_ill"] = int(ill.sum())
         worst = {"pixels": pix[idx][:5].tolist(), "dir": ang[idx][:5].tolist(),
                  "spread_dir": s_dir[:5].tolist(), "steps_changed": s_steps[:5].tolist()}
