@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import hh_inputs as hi
-from parity_util import (assert_parity_conditioned, export_volume, f32, gpu_trace,
+from parity_util import (angle, assert_parity_conditioned, export_volume, f32, gpu_trace,
                          ill_conditioned)
 
 pytestmark = pytest.mark.gpu
@@ -81,6 +81,35 @@ def test_fullsize_1080p_adaptive(gpu, oracle_lib, scene, theta):
     st = assert_parity_conditioned(got, ref, oracle_lib, {"kind": "grid", "vol4": vol4}, DIMS,
                                    cam, params, sel=pix)
     assert st["hits"] >= 1900
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_fullsize_1080p_whole_frame(gpu, oracle_lib, scene, storage):
+    """Every one of the 2,073,600 pixels of the 1080p frame against the
+    oracle (theta_max = 3e-5), with the conditioning rule over the whole
+    frame; prints the distribution of the exit-direction error, the rays
+    beyond tolerance and those leaving through another face."""
+    hh, torch = gpu
+    parts, parts_t, bg, bg_t = scene
+    vol = hh.hh_build_index_field(parts_t, hh.make_grid(DIMS, 2.0, storage), f32(hi.K_GD))
+    cam = f32(hi.orbit_camera(DIMS, 0.0, 0.0, 1920, 1080))
+    params = f32(hi.params_euler_adaptive(DIMS, theta_max=hi.THETA_CALIBRATED))
+    got = gpu_trace(hh, torch, vol, [cam], params, bg_t)[0]
+    vol4 = export_volume(hh, torch, vol, DIMS)
+    vol.close()
+    ref = oracle_lib.trace_grid(vol4, cam, params, bg, nthreads=16)
+    st = assert_parity_conditioned(got, ref, oracle_lib, {"kind": "grid", "vol4": vol4}, DIMS,
+                                   cam, params)
+    hit = (ref["flags"] & 1) != 0
+    ang = angle(got["exit_dir"][hit], ref["exit_dir"][hit])
+    q = np.percentile(ang, [50, 99, 99.9, 100])
+    print(f"1080p {storage}: {int(hit.sum())} hit rays; exit direction error median {q[0]:.2e}, "
+          f"p99 {q[1]:.2e}, p99.9 {q[2]:.2e}, max {q[3]:.2e} rad; {st['n_bad']} rays beyond "
+          f"tolerance ({st['n_ill']} ill conditioned); {st['step_mismatch']} with another step "
+          f"count; {st['face_mismatch']} through another face (exit points at most "
+          f"{st['face_mismatch_pos_max']:.1e} apart); RMSE {st['rmse']:.2e}")
+    assert st["hits"] == 876096
+    assert q[0] <= 1e-7  # the typical ray is well inside the tolerance
 
 
 def test_fullsize_8view_fp16(gpu, oracle_lib, scene):

@@ -1,0 +1,92 @@
+"""The parity rule itself (tests/parity_util.py), on the CPU: it accepts the
+oracle's own answer rounded to FP32, rejects mistakes planted on well- and on
+ill-conditioned rays, and its rounding model vanishes where the march has
+nothing to amplify."""
+import numpy as np
+import pytest
+
+import hh_inputs as hi
+from parity_util import (DIR_TOL, angle, assert_parity_conditioned, f32, ill_conditioned,
+                         path_spread, perturbation_spread, start_states)
+
+D = (64, 64, 64)
+
+
+@pytest.fixture(scope="module")
+def plume(oracle_lib):
+    parts = hi.plume_particles(16384, 64)
+    rho = oracle_lib.splat(parts, D, 2.0)
+    vol4 = oracle_lib.index_field(rho.astype(np.float32).astype(np.float64),
+                                  float(np.float32(hi.K_GD)))
+    cam = f32(hi.orbit_camera(D, 0.0, 0.0, 128, 128))
+    params = f32(hi.params_euler_adaptive(D, theta_max=hi.THETA_CALIBRATED))
+    ref = oracle_lib.trace_grid(vol4, cam, params, hi.checker_background(), nthreads=8)
+    return {"kind": "grid", "vol4": vol4}, cam, params, ref
+
+
+def _as_fp32(ref):
+    return {k: (v.astype(np.float32).astype(np.float64) if v.dtype == np.float64 else v.copy())
+            for k, v in ref.items()}
+
+
+def _turned(v, a, seed):
+    """v turned by the angle a about a seeded axis perpendicular to it."""
+    p = np.random.default_rng(seed).normal(size=3)
+    p -= np.dot(p, v) * v
+    p /= np.linalg.norm(p)
+    return np.cos(a) * v + np.sin(a) * p
+
+
+def test_accepts_the_oracle_rounded_to_fp32(oracle_lib, plume):
+    field, cam, params, ref = plume
+    st = assert_parity_conditioned(_as_fp32(ref), ref, oracle_lib, field, D, cam, params)
+    assert st["hits"] > 2000 and st["n_bad"] == 0
+
+
+def test_rejects_a_turned_well_conditioned_ray(oracle_lib, plume):
+    field, cam, params, ref = plume
+    hit = np.flatnonzero((ref["flags"] & 1) != 0)
+    C0, w0 = start_states(oracle_lib, cam, D, hit[:200])
+    s_dir, _, s_steps = perturbation_spread(oracle_lib, field, D, C0, w0, params)
+    # the direction perturbation alone moves the exit by 2^-23 rad
+    k = hit[:200][np.flatnonzero((s_dir < DIR_TOL / 4) & ~s_steps)[0]]
+    got = _as_fp32(ref)
+    got["exit_dir"][k] = _turned(ref["exit_dir"][k], 3 * DIR_TOL, seed=1)
+    assert angle(got["exit_dir"][k], ref["exit_dir"][k]) > 2 * DIR_TOL
+    with pytest.raises(AssertionError):
+        assert_parity_conditioned(got, ref, oracle_lib, field, D, cam, params)
+
+
+def test_rejects_an_ill_conditioned_ray_turned_far_beyond_its_spread(oracle_lib, plume):
+    field, cam, params, ref = plume
+    hit = np.flatnonzero((ref["flags"] & 1) != 0)
+    ill, s_dir, _, _ = ill_conditioned(oracle_lib, field, D, cam, params, hit)
+    if not ill.any():
+        pytest.skip("no ill-conditioned ray in this view")
+    i = int(np.argmax(s_dir))
+    C0, w0 = start_states(oracle_lib, cam, D, hit[i:i + 1])
+    p_dir, _, _ = path_spread(oracle_lib, field, D, C0, w0, params)
+    far = 100 * max(s_dir[i], p_dir[0]) + 1e-4  # beyond any one-step turn as well
+    got = _as_fp32(ref)
+    got["exit_dir"][hit[i]] = _turned(ref["exit_dir"][hit[i]], far, seed=2)
+    with pytest.raises(AssertionError):
+        assert_parity_conditioned(got, ref, oracle_lib, field, D, cam, params)
+
+
+def test_path_spread_vanishes_in_a_constant_field(oracle_lib, plume):
+    """With dn constant and g = 0 nothing bends the ray: the direction is
+    insensitive to rounding at every step, and the exit point moves only by
+    the position errors themselves (a random walk of half-ulp steps)."""
+    _, cam, params, ref = plume
+    vol4 = np.zeros(D[::-1] + (4,))
+    vol4[..., 0] = 1e-4
+    const = {"kind": "grid", "vol4": vol4}
+    hit = np.flatnonzero((ref["flags"] & 1) != 0)[:8]
+    C0, w0 = start_states(oracle_lib, cam, D, hit)
+    p_dir, p_pos, p_steps = path_spread(oracle_lib, const, D, C0, w0, params)
+    assert np.all(p_dir == 0.0)
+    K = np.array([oracle_lib.march_ray(const, D, C0[i], w0[i], params)["steps"]
+                  for i in range(len(hit))])
+    eps = 2.0**-24 * max(D)
+    assert np.all(p_pos > 0.0)
+    assert np.all(p_pos <= 3 * np.sqrt(K) * eps)
