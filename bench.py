@@ -105,6 +105,19 @@ def scene(wl: dict):
     return dims, parts, f32(cams), params, hi.checker_background()
 
 
+def steps_distribution(outs):
+    """Quantiles of the Eq. 16 step count over the rays that entered the volume
+    (outs: per-view dicts with device 'steps' and 'flags')."""
+    import torch
+
+    st = torch.cat([o["steps"][(o["flags"] & 1) != 0] for o in outs]).cpu().numpy()
+    if st.size == 0:
+        return None
+    q = np.percentile(st, [1, 10, 50, 90, 99])
+    return {"mean": round(float(st.mean()), 2), "p1": float(q[0]), "p10": float(q[1]),
+            "p50": float(q[2]), "p90": float(q[3]), "p99": float(q[4]), "max": int(st.max())}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -307,6 +320,26 @@ def run_ours(args):
     torch.cuda.synchronize()
     total_steps = sum(int(o["steps"].sum().item()) for o in stats)
     hits = sum(int((o["flags"] & 1).sum().item()) for o in stats)
+    steps_dist = steps_distribution(stats)
+    # the paper's theta_max = 3e-3 on the same volume and views (the schedule
+    # at which Eq. 18 keeps every step at h_max on this scene), frame only
+    theta_paper = None
+    if args.workload == "frame" and not args.no_compare:
+        p_paper = f32(hi.params_euler_adaptive(dims, theta_max=hi.THETA_PAPER))
+        with torch.cuda.stream(stream):
+            hh.hh_trace(vol, cams, p_paper, bg_t, stats, stream)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(10)]
+            for e0, e1 in evs:
+                flush.zero_()
+                e0.record(stream)
+                hh.hh_trace(vol, cams, p_paper, bg_t, stats, stream)
+                e1.record(stream)
+        torch.cuda.synchronize()
+        ms_paper = sum(a.elapsed_time(b) for a, b in evs) / len(evs)
+        theta_paper = {"theta_max": hi.THETA_PAPER, "march_ms": round(ms_paper, 4),
+                       "march_Mrays_s": round(n_rays / (ms_paper * 1e-3) / 1e6, 3),
+                       "steps_per_hit_ray": steps_distribution(stats)}
     outs = [{"rgb": o["rgb"]} for o in stats]
     del stats
 
@@ -461,6 +494,8 @@ def run_ours(args):
         "config": {"workload": wl["text"], "views": len(cams), "rays_per_step": n_rays,
                    "rays_hit": hits, "march_steps_per_frame": total_steps,
                    "steps_per_hit_ray": round(total_steps / max(hits, 1), 2),
+                   "steps_per_hit_ray_quantiles": steps_dist,
+                   "theta_paper": theta_paper,
                    "march_ms": round(ms_march, 4),
                    "build_ms": round(ms_step - ms_march, 4),
                    "march_Mrays_s": round(n_rays / (ms_march * 1e-3) / 1e6, 3),
@@ -701,7 +736,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
     ap.add_argument("--workload", default="frame", choices=sorted(WORKLOADS) + ["serve"])
     ap.add_argument("--no-compare", action="store_true",
-                    help="skip the per-view and FP32 comparison marches (multi-view workloads)")
+                    help="skip the comparison marches (per-view and FP32 for the multi-view "
+                         "workloads, theta_max = 3e-3 for the frame)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

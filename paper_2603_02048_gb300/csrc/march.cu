@@ -15,7 +15,8 @@
 //    bias B (hi = position + B, B above every coordinate and step), so every
 //    increment is smaller than hi and Fast2Sum is error-free; its rounding
 //    error goes to lo. The position proper is (hi - B) + lo, where hi - B is
-//    exact (Sterbenz).
+//    exact (Sterbenz); the volume is sampled, and the exit tested, at the
+//    lattice coordinate (hi - (B - 1/2)) + lo = position + 1/2, rounded once.
 //  - Divisions and square roots whose operands are far from any cancellation
 //    (ds / n, n theta / (|g_perp| + eps), the renormalisation term, |g_perp|)
 //    use the approximate hardware forms (relative error ~1e-7, harmless next
@@ -58,6 +59,8 @@ struct VolArgs {
     unsigned bx, bxy;   // BRICK2 bricks along x and per xy plane
     unsigned by8, bz8;  // BRICK2 strides (in elements) of one brick step in y and z
     float bias;         // power of two above every coordinate and step
+    float bias_u;       // bias - 1/2: (hi - bias_u) + lo is the lattice coordinate
+    float ux, uy, uz;   // n + 1/2: the far faces in lattice coordinates
     float h_fixed, h_min, h_max, theta, eps;
     int max_steps;
     const uint8_t* bg;
@@ -152,17 +155,17 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return r;
 }
 
-// Lattice cell and weight along one axis, in the halo coordinates of the
-// BRICK2 layout (the centre of grid voxel i at u = i + 1): u = p + 1/2,
-// i0 = floor(u), f = u - i0. A position p in [0, n] gives u in [0.5, n + 0.5],
-// so both corners i0, i0 + 1 lie in the padded axis [0, n + 1], and the halo
+// Lattice cell and weight along one axis from the lattice coordinate u =
+// position + 1/2, the halo coordinate of the BRICK2 layout (the centre of
+// grid voxel i at u = i + 1; the march carries u, not the position):
+// i0 = floor(u), f = u - i0. A position in [0, n] has u in [0.5, n + 0.5], so
+// both corners i0, i0 + 1 lie in the padded axis [0, n + 1], and the halo
 // copies make this the sample with the lattice coordinate clamped to the
-// voxel centres. The Euler march samples only accepted positions, which lie
-// in the box (a NaN position gives i0 = 0); CLAMP first clamps u to
-// [0.5, n + 0.5] (NaN to 0.5) for RK4 stage points, which may lie outside.
+// voxel centres. The Euler march samples only accepted points, which lie in
+// the box (a NaN gives i0 = 0); CLAMP first clamps u to [0.5, n + 0.5] (NaN
+// to 0.5) for RK4 stage points, which may lie outside.
 template <bool CLAMP>
-__device__ __forceinline__ void axis_cell(float p, int n, int& i0, float& f) {
-    float u = p + 0.5f;
+__device__ __forceinline__ void axis_cell(float u, int n, int& i0, float& f) {
     if (CLAMP) u = fminf(fmaxf(u, 0.5f), static_cast<float>(n) + 0.5f);
     const float fl = floorf(u);
     i0 = static_cast<int>(fl);
@@ -179,16 +182,16 @@ __device__ __forceinline__ float4 ld_fp16(const ushort4* __restrict__ v, unsigne
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
-// Trilinear sample of {dn, g} at p (Sec. 3.3.1: n and grad n sampled with
-// trilinear interpolation); FP16 volumes are interpolated as stored and
-// scaled once afterwards.
+// Trilinear sample of {dn, g} at lattice coordinate u = position + 1/2
+// (Sec. 3.3.1: n and grad n sampled with trilinear interpolation); FP16
+// volumes are interpolated as stored and scaled once afterwards.
 template <int STORAGE, bool CLAMP>
-__device__ __forceinline__ Sample fetch(const VolArgs& A, float3 p) {
+__device__ __forceinline__ Sample fetch(const VolArgs& A, float3 u) {
     int ix, iy, iz;
     float fx, fy, fz;
-    axis_cell<CLAMP>(p.x, A.nx, ix, fx);
-    axis_cell<CLAMP>(p.y, A.ny, iy, fy);
-    axis_cell<CLAMP>(p.z, A.nz, iz, fz);
+    axis_cell<CLAMP>(u.x, A.nx, ix, fx);
+    axis_cell<CLAMP>(u.y, A.ny, iy, fy);
+    axis_cell<CLAMP>(u.z, A.nz, iz, fz);
     // BRICK2 element of corner (ix, iy, iz), then the steps to the other
     // corners: +1 in x stays in the brick (slot +1) when ix is even, else it
     // moves to the next brick (slot -1, brick +1: +7); likewise y (+2 or
@@ -284,10 +287,12 @@ __device__ __forceinline__ float step_length(const VolArgs& A, float n, float gp
 // it is, as FP32 normalisation would); r only scales w1, never turns it, and
 // its error is undone at the next step. Only d is carried, so the rounding of
 // the update never touches the O(1) part w_ref.
-__device__ __forceinline__ float3 renormalize(float3 w1, float3 d1) {
+__device__ __forceinline__ float renorm_term(float3 w1) {
     const float e = fmaf(w1.x, w1.x, fmaf(w1.y, w1.y, fmaf(w1.z, w1.z, -1.0f)));
-    const float rm1 = e * fmaf(e, fmaf(-0.3125f, e, 0.375f), -0.5f);
-    return fma3(rm1, w1, d1);
+    return e * fmaf(e, fmaf(-0.3125f, e, 0.375f), -0.5f);
+}
+__device__ __forceinline__ float3 renormalize(float3 w1, float3 d1) {
+    return fma3(renorm_term(w1), w1, d1);
 }
 
 // Colour of direction d in the equirect environment map (bilinear, u wraps,
@@ -413,9 +418,10 @@ __device__ __forceinline__ bool slab(const VolArgs& A, float3 o, float3 d, float
     return tout >= fmaxf(tin, 0.0f);
 }
 
-__device__ __forceinline__ bool outside(const VolArgs& A, float3 p) {
-    return p.x < 0.0f || p.y < 0.0f || p.z < 0.0f || p.x > static_cast<float>(A.nx) ||
-           p.y > static_cast<float>(A.ny) || p.z > static_cast<float>(A.nz);
+// Whether lattice coordinate u = position + 1/2 lies outside the box
+// (position outside [0, n] on some axis).
+__device__ __forceinline__ bool outside(const VolArgs& A, float3 u) {
+    return u.x < 0.5f || u.y < 0.5f || u.z < 0.5f || u.x > A.ux || u.y > A.uy || u.z > A.uz;
 }
 
 // Fraction tau in [0, 1] of the increment `inc` from (hi + lo) at which the
@@ -436,9 +442,9 @@ __device__ __forceinline__ float exit_fraction(const VolArgs& A, float3 hi, floa
 }
 
 template <int STORAGE, bool CLAMP>
-__device__ __forceinline__ float3 perp_rate(const VolArgs& A, float3 p, float3 w, float& n,
+__device__ __forceinline__ float3 perp_rate(const VolArgs& A, float3 u, float3 w, float& n,
                                             float& gperp_norm) {
-    const Sample s = fetch<STORAGE, CLAMP>(A, p);
+    const Sample s = fetch<STORAGE, CLAMP>(A, u);
     n = 1.0f + s.dn;
     const float3 g = make_float3(s.gx, s.gy, s.gz);
     const float3 gp = fma3(-dot(w, g), w, g);
@@ -447,8 +453,9 @@ __device__ __forceinline__ float3 perp_rate(const VolArgs& A, float3 p, float3 w
 }
 
 // Per-ray state of the march: primary direction w_ref, deflection d, biased
-// compensated position (hi, lo) with its rounded value c = (hi - B) + lo,
-// steps taken and flags.
+// compensated position (hi, lo) (position = (hi - B) + lo), its lattice
+// coordinate rounded once, c = (hi - (B - 1/2)) + lo = position + 1/2 (where
+// the volume is sampled and the exit is tested), steps taken and flags.
 struct RayState {
     float3 wr, hi, lo, d, c;
     int k;
@@ -490,8 +497,8 @@ __device__ __forceinline__ void ray_begin(const VolArgs& V, const ViewArgs& C, i
         fast_two_sum(V.bias, entry.y, R.hi.y, R.lo.y);
         fast_two_sum(V.bias, entry.z, R.hi.z, R.lo.z);
     }
-    R.c = make_float3((R.hi.x - V.bias) + R.lo.x, (R.hi.y - V.bias) + R.lo.y,
-                      (R.hi.z - V.bias) + R.lo.z);
+    R.c = make_float3((R.hi.x - V.bias_u) + R.lo.x, (R.hi.y - V.bias_u) + R.lo.y,
+                      (R.hi.z - V.bias_u) + R.lo.z);
 }
 
 // One step of Eq. 16 (or RK4) with the Eq. 18 (or fixed) step length.
@@ -503,7 +510,7 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     const float3 wr = R.wr, d = R.d;
     const float3 C = R.c;
     float ds;
-    float3 dnew, wnew, inc;
+    float3 dnew, inc;
     if (STEPPER == HH_STEP_RK4) {
         float n1, gpn, n2, n3, n4, unused;
         const float3 w1 = wr + d;
@@ -526,7 +533,6 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
         const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
         const float3 dsum = fma3(ds * (1.0f / 6.0f), ksum, d);
         dnew = renormalize(wr + dsum, dsum);
-        wnew = wr + dnew;
         const float3 dpos = (1.0f / 6.0f) * (d + 2.0f * (d2 + d3) + d4);
         inc = ds * (wr + dpos);
     } else {
@@ -535,16 +541,20 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
         const float3 gp = perp_rate<STORAGE, false>(V, C, w, n, gpn);
         ds = step_length<ADAPTIVE>(V, n, gpn);
         const float3 d1 = fma3(__fdividef(ds, n), gp, d);
-        dnew = renormalize(wr + d1, d1);
-        wnew = wr + dnew;
-        inc = ds * wnew;
+        // Eq. 16: w' = normalize(w1), C' = C + ds w'; with w' = (1 + r) w1
+        // the increment is ds (1 + r) w1 (w' itself is formed only at the exit)
+        const float3 w1 = wr + d1;
+        const float rm1 = renorm_term(w1);
+        dnew = fma3(rm1, w1, d1);
+        inc = fmaf(ds, rm1, ds) * w1;
     }
     float3 nhi, err;
     fast_two_sum(R.hi.x, inc.x, nhi.x, err.x);
     fast_two_sum(R.hi.y, inc.y, nhi.y, err.y);
     fast_two_sum(R.hi.z, inc.z, nhi.z, err.z);
     const float3 nlo = R.lo + err;
-    const float3 P = make_float3((nhi.x - B) + nlo.x, (nhi.y - B) + nlo.y, (nhi.z - B) + nlo.z);
+    const float Bu = V.bias_u;
+    const float3 P = make_float3((nhi.x - Bu) + nlo.x, (nhi.y - Bu) + nlo.y, (nhi.z - Bu) + nlo.z);
     ++R.k;
     const float3 ohi = R.hi, olo = R.lo;
     R.hi = nhi;
@@ -555,7 +565,7 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
         const float3 h0 = make_float3(ohi.x - B, ohi.y - B, ohi.z - B);  // exact
         const float tau = exit_fraction(V, h0, olo, inc);
         ep = h0 + fma3(tau, inc, olo);
-        ed = wnew;
+        ed = wr + dnew;
         R.flags |= HH_FLAG_EXITED;
         return true;
     }
@@ -578,7 +588,8 @@ __device__ __forceinline__ void ray_end(const VolArgs& V, const ViewArgs& C, int
         ed = R.wr;
     } else if (!(flags & HH_FLAG_EXITED)) {
         flags |= HH_FLAG_MAXSTEPS;
-        ep = R.c;
+        ep = make_float3((R.hi.x - V.bias) + R.lo.x, (R.hi.y - V.bias) + R.lo.y,
+                         (R.hi.z - V.bias) + R.lo.z);
         ed = R.wr + R.d;
     }
     const float3 rgb = scene_color(V, ep, ed);
@@ -810,14 +821,19 @@ VolArgs make_vol_args(const hh_volume_s* vol, const hh_step_params& P, const hh_
     A.bxy = vol->bxy;
     A.by8 = vol->bx * 8u;
     A.bz8 = vol->bxy * 8u;
-    // bias: a power of two B with B >= 2 * step and B >= extent + step, so
-    // positions in [-step, extent + step] keep hi in [B/2, 2B]
+    // bias: a power of two B with B >= 2 * step and B >= extent + step + 1, so
+    // positions in [-step, extent + step] keep hi in [B/2, 2B - 1] and both
+    // hi - B and hi - (B - 1/2) are exact (Sterbenz)
     const float step = P.adaptive ? P.h_max : P.h_fixed;
     const float need =
-        fmaxf(static_cast<float>(max(vol->nx, max(vol->ny, vol->nz))) + step, 2.0f * step);
+        fmaxf(static_cast<float>(max(vol->nx, max(vol->ny, vol->nz))) + step + 1.0f, 2.0f * step);
     float B = 8.0f;
     while (B < need) B *= 2.0f;
     A.bias = B;
+    A.bias_u = B - 0.5f;
+    A.ux = static_cast<float>(vol->nx) + 0.5f;
+    A.uy = static_cast<float>(vol->ny) + 0.5f;
+    A.uz = static_cast<float>(vol->nz) + 0.5f;
     A.h_fixed = P.h_fixed;
     A.h_min = P.h_min;
     A.h_max = P.h_max;
