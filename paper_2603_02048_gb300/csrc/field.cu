@@ -12,7 +12,9 @@
 // The packed volume is written in the volume's layout (BRICK2 with its halo
 // of edge copies for volumes the march reads, LINEAR for the allocation-free
 // build's caller buffer); in BRICK2 the x-pairs of a warp land in whole
-// 32-byte sectors.
+// 32-byte sectors. The volume stores are marked evict-first (st.global.cs):
+// the volume outgrows L2 anyway, and this keeps the density, which the
+// kernel is still reading, resident in L2 instead.
 #include "hh_internal.h"
 
 namespace hh {
@@ -97,8 +99,8 @@ __global__ void __launch_bounds__(256, MODE == 2 ? 5 : 8) field_column_kernel(co
             const size_t oh = zh ? brick2_offset(I, J, k == 0 ? 0 : nz + 1, L.bx, L.bxy) : 0;
             if (MODE == 0) {
                 const float4 v = make_float4(e.dn, e.gx, e.gy, e.gz);
-                static_cast<float4*>(out)[o] = v;
-                if (zh) static_cast<float4*>(out)[oh] = v;
+                __stcs(static_cast<float4*>(out) + o, v);
+                if (zh) __stcs(static_cast<float4*>(out) + oh, v);
             } else if (MODE == 1) {
                 mn = fmaxf(mn, fabsf(e.dn));
                 mg = fmaxf(mg, fmaxf(fabsf(e.gx), fmaxf(fabsf(e.gy), fabsf(e.gz))));
@@ -108,8 +110,10 @@ __global__ void __launch_bounds__(256, MODE == 2 ? 5 : 8) field_column_kernel(co
                 q.y = __half_as_ushort(__float2half_rn(e.gx / s_g));
                 q.z = __half_as_ushort(__float2half_rn(e.gy / s_g));
                 q.w = __half_as_ushort(__float2half_rn(e.gz / s_g));
-                static_cast<ushort4*>(out)[o] = q;
-                if (zh) static_cast<ushort4*>(out)[oh] = q;
+                const uint2 w = make_uint2(static_cast<unsigned>(q.x) | (static_cast<unsigned>(q.y) << 16),
+                                           static_cast<unsigned>(q.z) | (static_cast<unsigned>(q.w) << 16));
+                __stcs(static_cast<uint2*>(out) + o, w);
+                if (zh) __stcs(static_cast<uint2*>(out) + oh, w);
             }
             dprev = dcur;
             dcur = dnext;
