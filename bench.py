@@ -392,8 +392,9 @@ def run_ours(args):
     ms_step = max_over_ranks(dist, sum(step_ms) / len(step_ms), dev)
     ms_march = sum(march_ms) / len(march_ms)
 
-    # end to end through the C ABI: pinned host particles in, the display
-    # images (rgb8: what a viewer shows) out, every step
+    # end to end one frame at a time (reported as e2e.serial): pinned host
+    # particles in, the display images (rgb8: what a viewer shows) out, every
+    # step, each step synchronised and timed with CUDA events
     host_parts = torch.from_numpy(parts).pin_memory()
     outs8 = [{"rgb8": torch.empty(o["rgb"].numel(), dtype=torch.uint8, device=dev)} for o in outs]
     host_rgb8 = [torch.empty(o["rgb8"].numel(), dtype=torch.uint8).pin_memory() for o in outs8]
@@ -422,7 +423,35 @@ def run_ours(args):
                 e2e_ms.append(a.elapsed_time(b))
     if batch8 is not None:
         batch8.close()
-    ms_e2e = max_over_ranks(dist, sum(e2e_ms) / max(len(e2e_ms), 1), dev)
+    ms_e2e_serial = max_over_ranks(dist, sum(e2e_ms) / max(len(e2e_ms), 1), dev)
+
+    # end to end through the C ABI with host buffers: the frame pipeline
+    # (hh_pipeline_*), pinned host particles in and every view's display image
+    # out each step, two frames in flight (uploads and downloads overlap the
+    # kernels of the neighbouring frames); host wall clock over the K steps
+    ms_e2e = None
+    if not args.no_e2e:
+        pipe = hh.hh_pipeline_create(grid, K_GD32, len(parts), cams, params, bg_t,
+                                     tuned if batch is not None else None)
+        host_img = [[torch.empty(c["width"] * c["height"] * 3, dtype=torch.uint8).pin_memory()
+                     for c in cams] for _ in range(2)]
+
+        def run_pipeline(n):
+            ids = []
+            for k in range(n):
+                ids.append(hh.hh_pipeline_submit(pipe, host_parts, host_img[k % 2]))
+                if k >= 1:
+                    hh.hh_pipeline_wait(pipe, ids[-2])
+            hh.hh_pipeline_wait(pipe, ids[-1])
+
+        run_pipeline(args.warmup)
+        torch.cuda.synchronize()
+        barrier(dist)
+        t0 = time.perf_counter()
+        run_pipeline(args.steps)
+        ms_pipe = (time.perf_counter() - t0) * 1e3 / args.steps
+        pipe.close()
+        ms_e2e = max_over_ranks(dist, ms_pipe, dev)
 
     # comparisons for the multi-view workloads: the same views as per-view
     # hh_trace launches on this volume, and the plain FP32 single-view march
@@ -504,7 +533,14 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": None if args.no_e2e else {
             "value": round(world * n_rays / (ms_e2e * 1e-3) / 1e6, 3), "unit": "Mrays/s",
-            "ms_per_step": round(ms_e2e, 4), "h2d_bytes_per_step": int(parts.nbytes),
+            "ms_per_step": round(ms_e2e, 4), "api": "hh_pipeline_submit / hh_pipeline_wait "
+            "(host buffers, two frames in flight, host wall clock, L2 not flushed: every step "
+            "rewrites the volume)",
+            "serial": {"value": round(world * n_rays / (ms_e2e_serial * 1e-3) / 1e6, 3),
+                       "ms_per_step": round(ms_e2e_serial, 4),
+                       "api": "one frame at a time: pinned copy in, hh_volume_rebuild, "
+                              "hh_trace or batch launch, copy out; CUDA events, L2 flushed"},
+            "h2d_bytes_per_step": int(parts.nbytes),
             "d2h_bytes_per_step": int(n_rays * 3), "output": "rgb8 display images"},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,

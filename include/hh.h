@@ -303,6 +303,60 @@ hh_status hh_batch_launch_graph(hh_batch b, void* stream);
 hh_status hh_batch_free(hh_batch b);
 
 /* ---------------------------------------------------------------------- */
+/* Real-time frame pipeline: host particles in, host display images out    */
+/* ---------------------------------------------------------------------- */
+
+/* The per-frame loop of the paper's renderer (Sec. 3.3: each simulation
+ * frame's particles splatted into the index volume, Sec. 3.3.1, then every
+ * camera's view marched through it, Secs. 3.3.2-3.3.3), with the particles
+ * coming from host memory and the display images (RGB8, as in hh_view_out)
+ * going back to host memory. Frames are double buffered on three streams of
+ * the library's own: while frame t is built and marched, frame t+1's
+ * particles are uploaded and frame t-1's images downloaded, so the copies
+ * overlap the kernels. One thread drives a pipeline. */
+typedef struct hh_pipeline_s* hh_pipeline;
+
+/* Creates a pipeline for the views cams[0..n_cams) (1..4096) of a volume on
+ * `grid` (h_kernel > 0) with Gladstone-Dale constant K_gd, for up to
+ * max_particles particles per frame. cfg NULL: one hh_trace launch per view;
+ * otherwise the views run as one batched launch (hh_batch, bit-identical to
+ * hh_trace) with that configuration, replayed from a CUDA graph. Allocates
+ * on the current device the volume, two particle buffers and two sets of
+ * image buffers; cams and params are copied; the background's device
+ * buffers stay owned by the caller and must outlive the pipeline.
+ * Synchronous. */
+hh_status hh_pipeline_create(const hh_grid* grid, float K_gd, int64_t max_particles,
+                             const hh_camera* cams, int n_cams, const hh_step_params* params,
+                             const hh_background* bg, const hh_batch_config* cfg,
+                             hh_pipeline* out);
+
+/* Enqueues frame t (its number, counting from 0, in *frame): upload of the
+ * n particles (float4 {x, y, z, m} in voxel units) at xyzm_host, volume
+ * rebuild (hh_volume_rebuild), the march of every view, and the download of
+ * view i's H*W*3 bytes to rgb8_host[i]. Returns once the frame is enqueued;
+ * it first waits for frame t-2 to finish (HH_ERR_TIMEOUT after 60 s), so at
+ * most two frames are in flight. The host buffers must stay valid, and
+ * xyzm_host unchanged, until hh_pipeline_wait(t) returns. Page-locked host
+ * memory (cudaHostAlloc) lets the copies run asynchronously; with pageable
+ * memory the copies still work but block the calling thread. */
+hh_status hh_pipeline_submit(hh_pipeline p, const float* xyzm_host, int64_t n,
+                             uint8_t* const* rgb8_host, uint64_t* frame);
+
+/* Waits, at most timeout_ms (HH_ERR_TIMEOUT after), until frame's images
+ * are in host memory. HH_ERR_NOT_FOUND for a frame not yet submitted; a
+ * frame two or more behind the last submitted one is complete. */
+hh_status hh_pipeline_wait(hh_pipeline p, uint64_t frame, int timeout_ms);
+
+/* The pipeline's volume (owned by the pipeline, valid until
+ * hh_pipeline_free); once frame t has been waited for and no later frame
+ * submitted, it holds frame t's volume. */
+hh_status hh_pipeline_volume(hh_pipeline p, hh_volume* vol);
+
+/* Waits (bounded, 60 s per frame) for the submitted frames and releases the
+ * pipeline; HH_ERR_TIMEOUT leaves it allocated. NULL is ok. */
+hh_status hh_pipeline_free(hh_pipeline p);
+
+/* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of render requests                         */
 /* ---------------------------------------------------------------------- */
 

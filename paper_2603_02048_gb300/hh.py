@@ -15,6 +15,13 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libhh.so")
 
 HH_OK = 0
+HH_ERR_INVALID_ARG = 1
+HH_ERR_OOM = 2
+HH_ERR_CUDA = 3
+HH_ERR_TIMEOUT = 4
+HH_ERR_BUSY = 5
+HH_ERR_CANCELLED = 6
+HH_ERR_NOT_FOUND = 7
 STATUS_NAMES = {0: "HH_OK", 1: "HH_ERR_INVALID_ARG", 2: "HH_ERR_OOM", 3: "HH_ERR_CUDA",
                 4: "HH_ERR_TIMEOUT", 5: "HH_ERR_BUSY", 6: "HH_ERR_CANCELLED",
                 7: "HH_ERR_NOT_FOUND"}
@@ -135,6 +142,16 @@ SIGNATURES = {
     "hh_batch_launch": (ctypes.c_int, [_P, _P]),
     "hh_batch_launch_graph": (ctypes.c_int, [_P, _P]),
     "hh_batch_free": (ctypes.c_int, [_P]),
+    "hh_pipeline_create": (ctypes.c_int, [ctypes.POINTER(hh_grid), ctypes.c_float, ctypes.c_int64,
+                                          ctypes.POINTER(hh_camera), ctypes.c_int,
+                                          ctypes.POINTER(hh_step_params),
+                                          ctypes.POINTER(hh_background),
+                                          ctypes.POINTER(hh_batch_config), ctypes.POINTER(_P)]),
+    "hh_pipeline_submit": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(_P),
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "hh_pipeline_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int]),
+    "hh_pipeline_volume": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "hh_pipeline_free": (ctypes.c_int, [_P]),
     "hh_serve_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_P)]),
     "hh_serve_set_config": (ctypes.c_int, [_P, ctypes.POINTER(hh_batch_config)]),
     "hh_serve_put_volume": (ctypes.c_int, [_P, ctypes.c_int64, _P]),
@@ -432,6 +449,99 @@ def hh_batch_launch_graph(b: Batch, stream=None):
 
 def hh_batch_free(b: Batch):
     b.close()
+
+
+class Pipeline:
+    """Owns an hh_pipeline handle; keeps the background alive, and each
+    frame's host buffers until the frame has been waited for."""
+
+    def __init__(self, handle: ctypes.c_void_p, n_views: int, keep):
+        self.handle = handle
+        self.n_views = n_views
+        self._keep = keep
+        self._frames = {}  # frame -> its host buffers
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            _check(load().hh_pipeline_free(self.handle))
+        self.handle = None
+        self._frames.clear()
+
+    def __del__(self):
+        try:
+            if self.handle is not None and self.handle.value:
+                load().hh_pipeline_free(self.handle)
+        except Exception:
+            pass
+
+
+def _host_ptr(a):
+    """Address of a contiguous host array: a CPU torch tensor (pinned for
+    asynchronous copies) or a numpy array."""
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("expected a contiguous host (CPU) tensor")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def hh_pipeline_create(grid: hh_grid, K_gd: float, max_particles: int, cams, params, bg,
+                       cfg=None) -> Pipeline:
+    """cfg: None (one hh_trace launch per view) or a dict of hh_batch_config
+    fields (the views as one batched launch)."""
+    n, c_cams, _ = _views(cams, [{} for _ in cams])
+    P = params if isinstance(params, hh_step_params) else make_params(params)
+    B = _background(bg)
+    C = None if cfg is None else ctypes.byref(hh_batch_config(
+        int(cfg["block_threads"]), int(cfg["blocks_per_sm"]), int(cfg["refill_min"]),
+        int(cfg["tile_w"])))
+    out = ctypes.c_void_p()
+    _check(load().hh_pipeline_create(ctypes.byref(grid), float(K_gd), int(max_particles), c_cams,
+                                     n, ctypes.byref(P), ctypes.byref(B), C, ctypes.byref(out)))
+    return Pipeline(out, n, (bg, B))
+
+
+def hh_pipeline_submit(p: Pipeline, xyzm_host, rgb8_host) -> int:
+    """xyzm_host: (n, 4) float32 host array; rgb8_host: one host uint8 array
+    of H*W*3 bytes per view. Returns the frame number."""
+    if len(rgb8_host) != p.n_views:
+        raise ValueError(f"expected {p.n_views} image buffers")
+    n = int(xyzm_host.shape[0]) if len(xyzm_host.shape) else 0
+    imgs = (ctypes.c_void_p * p.n_views)(*[_host_ptr(a) for a in rgb8_host])
+    frame = ctypes.c_uint64()
+    _check(load().hh_pipeline_submit(p.handle, _host_ptr(xyzm_host) if n else None, n, imgs,
+                                     ctypes.byref(frame)))
+    p._frames[frame.value] = (xyzm_host, rgb8_host)
+    return frame.value
+
+
+def hh_pipeline_wait(p: Pipeline, frame: int, timeout_ms: int = 60000):
+    _check(load().hh_pipeline_wait(p.handle, int(frame), int(timeout_ms)))
+    for f in [f for f in p._frames if f <= frame]:
+        del p._frames[f]
+
+
+def hh_pipeline_volume(p: Pipeline) -> Volume:
+    """The pipeline's own volume (not owned: do not close it)."""
+    out = ctypes.c_void_p()
+    _check(load().hh_pipeline_volume(p.handle, ctypes.byref(out)))
+    return _BorrowedVolume(out)
+
+
+class _BorrowedVolume(Volume):
+    """A volume handle owned by someone else (close() and collection leave it)."""
+
+    def close(self):
+        self.handle = None
+
+    def __del__(self):
+        pass
+
+
+def hh_pipeline_free(p: Pipeline):
+    p.close()
 
 
 class Server:
