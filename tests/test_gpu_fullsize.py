@@ -210,3 +210,67 @@ def test_fullsize_512_fp16_32_views_batched(gpu, oracle_lib):
     # ill-conditioned rays grows with them: no more rays are excused than the
     # oracle itself finds ill conditioned in the sample
     assert ill <= pop_ill + 2
+
+
+def test_fullsize_serve_384_fp16(gpu, oracle_lib):
+    """The serving configuration at full size: 384^3 FP16 volumes of the
+    1,048,576-particle drifting plume, the first requests of the seeded
+    Poisson stream (1-16 views up to 3840x2160) in flight together. Every
+    served display image is hh_trace's on the same volume, bit for bit; the
+    first request is checked against the FP64 oracle on sampled pixels."""
+    hh, torch = gpu
+    L3 = 384
+    dims = (L3, L3, L3)
+    base = hi.plume_particles(1048576, L3)
+    vols = []
+    for t in range(3):
+        parts_t = torch.from_numpy(hi.drifting_plume_frame(base, t, L=L3)).cuda()
+        vols.append(hh.hh_build_index_field(parts_t, hh.make_grid(dims, 2.0, "fp16"),
+                                            f32(hi.K_GD)))
+    del parts_t
+    params = f32(hi.params_euler_adaptive(dims, theta_max=hi.THETA_CALIBRATED))
+    bg = hi.checker_background()
+    bg_t = torch.from_numpy(bg).cuda()
+    srv = hh.hh_serve_create(8 << 30, 8)
+    for t, v in enumerate(vols):
+        hh.hh_serve_put_volume(srv, t, v)
+    reqs = hi.serving_requests()[:6]
+    tickets = []
+    for i, r in enumerate(reqs):
+        cams = f32([hi.orbit_camera(dims, az, el, w, h) for az, el, w, h in r["views"]])
+        outputs = (hh.HH_OUT_RGB | hh.HH_OUT_EXIT | hh.HH_OUT_STEPS | hh.HH_OUT_RGB8) if i == 0 \
+            else hh.HH_OUT_RGB8
+        # the stream's first requests all fall in sim frame 0: spread them
+        # over the three volumes
+        tickets.append((hh.hh_serve_submit(srv, i % 3, cams, params, bg_t, outputs), i % 3,
+                        cams))
+    n_views = 0
+    first = None
+    for ti, (tk, f, cams) in enumerate(tickets):
+        hh.hh_serve_wait(srv, tk, 120000)
+        ref = [{"rgb8": torch.empty(c["width"] * c["height"] * 3, dtype=torch.uint8,
+                                    device="cuda")} for c in cams]
+        hh.hh_trace(vols[f], cams, params, bg_t, ref)
+        torch.cuda.synchronize()
+        for i, c in enumerate(cams):
+            v = hh.hh_serve_view(srv, tk, i, c["width"], c["height"])
+            assert torch.equal(v["rgb8"], ref[i]["rgb8"]), (ti, i)
+            if ti == 0 and i == 0:
+                first = {k: (t.cpu().numpy().reshape(-1, 3).astype(np.float64)
+                             if k in ("rgb", "exit_pos", "exit_dir")
+                             else t.cpu().numpy().view(np.uint32) if k == "flags"
+                             else t.cpu().numpy()) for k, t in v.items() if k != "rgb8"}
+            n_views += 1
+        hh.hh_serve_release(srv, tk)
+    assert n_views >= 12
+    srv.close()
+    # the first request's first view against the oracle
+    _, f, cams = tickets[0]
+    vol4 = export_volume(hh, torch, vols[f], dims)
+    for v in vols:
+        v.close()
+    pix = _sample_pixels(cams[0], 400, seed=500, flags=first["flags"])
+    ref = oracle_lib.trace_grid(vol4, cams[0], params, bg, pixels=pix, nthreads=16)
+    st = assert_parity_conditioned(first, ref, oracle_lib, {"kind": "grid", "vol4": vol4}, dims,
+                                   cams[0], params, sel=pix)
+    assert st["hits"] >= 100
