@@ -186,7 +186,7 @@ __device__ __forceinline__ float4 ld_fp16(const ushort4* __restrict__ v, unsigne
 // (Sec. 3.3.1: n and grad n sampled with trilinear interpolation); FP16
 // volumes are interpolated as stored and scaled once afterwards.
 template <int STORAGE, bool CLAMP>
-__device__ __forceinline__ Sample fetch(const VolArgs& A, float3 u) {
+__device__ __forceinline__ Sample fetch(const VolArgs& A, float3 u, float s_n, float s_g) {
     int ix, iy, iz;
     float fx, fy, fz;
     axis_cell<CLAMP>(u.x, A.nx, ix, fx);
@@ -262,7 +262,6 @@ __device__ __forceinline__ Sample fetch(const VolArgs& A, float3 u) {
         s.gy = c.z;
         s.gz = c.w;
     } else {
-        const float s_n = __ldg(A.scales), s_g = __ldg(A.scales + 1);
         s.dn = c.x * s_n;
         s.gx = c.y * s_g;
         s.gy = c.z * s_g;
@@ -442,9 +441,9 @@ __device__ __forceinline__ float exit_fraction(const VolArgs& A, float3 hi, floa
 }
 
 template <int STORAGE, bool CLAMP>
-__device__ __forceinline__ float3 perp_rate(const VolArgs& A, float3 u, float3 w, float& n,
-                                            float& gperp_norm) {
-    const Sample s = fetch<STORAGE, CLAMP>(A, u);
+__device__ __forceinline__ float3 perp_rate(const VolArgs& A, float3 u, float3 w, float s_n,
+                                            float s_g, float& n, float& gperp_norm) {
+    const Sample s = fetch<STORAGE, CLAMP>(A, u, s_n, s_g);
     n = 1.0f + s.dn;
     const float3 g = make_float3(s.gx, s.gy, s.gz);
     const float3 gp = fma3(-dot(w, g), w, g);
@@ -460,6 +459,7 @@ struct RayState {
     float3 wr, hi, lo, d, c;
     int k;
     uint32_t flags;
+    float sn, sg;  // the volume's FP16 scales, read once per ray
 };
 
 // Pixel (x, y) of slot p (0..31) of a tile_w x (32 / tile_w) warp tile. Each
@@ -479,6 +479,8 @@ __device__ __forceinline__ void tile_pixel(int p, int tile_w_log2, int& x, int& 
 __device__ __forceinline__ void ray_begin(const VolArgs& V, const ViewArgs& C, int px, int py,
                                           RayState& R) {
     R.wr = primary_ray(C, px, py);
+    R.sn = __ldg(V.scales);
+    R.sg = __ldg(V.scales + 1);
     R.k = 0;
     R.flags = 0;
     R.d = make_float3(0.0f, 0.0f, 0.0f);
@@ -514,21 +516,21 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     if (STEPPER == HH_STEP_RK4) {
         float n1, gpn, n2, n3, n4, unused;
         const float3 w1 = wr + d;
-        const float3 gp1 = perp_rate<STORAGE, true>(V, C, w1, n1, gpn);
+        const float3 gp1 = perp_rate<STORAGE, true>(V, C, w1, R.sn, R.sg, n1, gpn);
         ds = step_length<ADAPTIVE>(V, n1, gpn);
         const float hds = 0.5f * ds;
         const float3 k1 = __fdividef(1.0f, n1) * gp1;
         const float3 d2 = fma3(hds, k1, d);
         const float3 w2 = wr + d2;
-        const float3 gp2 = perp_rate<STORAGE, true>(V, fma3(hds, w1, C), w2, n2, unused);
+        const float3 gp2 = perp_rate<STORAGE, true>(V, fma3(hds, w1, C), w2, R.sn, R.sg, n2, unused);
         const float3 k2 = __fdividef(1.0f, n2) * gp2;
         const float3 d3 = fma3(hds, k2, d);
         const float3 w3 = wr + d3;
-        const float3 gp3 = perp_rate<STORAGE, true>(V, fma3(hds, w2, C), w3, n3, unused);
+        const float3 gp3 = perp_rate<STORAGE, true>(V, fma3(hds, w2, C), w3, R.sn, R.sg, n3, unused);
         const float3 k3 = __fdividef(1.0f, n3) * gp3;
         const float3 d4 = fma3(ds, k3, d);
         const float3 w4 = wr + d4;
-        const float3 gp4 = perp_rate<STORAGE, true>(V, fma3(ds, w3, C), w4, n4, unused);
+        const float3 gp4 = perp_rate<STORAGE, true>(V, fma3(ds, w3, C), w4, R.sn, R.sg, n4, unused);
         const float3 k4 = __fdividef(1.0f, n4) * gp4;
         const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
         const float3 dsum = fma3(ds * (1.0f / 6.0f), ksum, d);
@@ -538,7 +540,7 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     } else {
         float n, gpn;
         const float3 w = wr + d;
-        const float3 gp = perp_rate<STORAGE, false>(V, C, w, n, gpn);
+        const float3 gp = perp_rate<STORAGE, false>(V, C, w, R.sn, R.sg, n, gpn);
         ds = step_length<ADAPTIVE>(V, n, gpn);
         const float3 d1 = fma3(__fdividef(ds, n), gp, d);
         // Eq. 16: w' = normalize(w1), C' = C + ds w'; with w' = (1 + r) w1
