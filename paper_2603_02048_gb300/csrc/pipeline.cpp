@@ -52,6 +52,19 @@ cudaError_t wait_event(cudaEvent_t ev, int timeout_ms) {
     }
 }
 
+// Makes `device` current for the scope and restores the caller's device.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int device) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != device) cudaSetDevice(device);
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
 
 struct hh_pipeline_s {
@@ -180,7 +193,7 @@ hh_status hh_pipeline_submit(hh_pipeline p, const float* xyzm_host, int64_t n,
         if (!rgb8_host[v]) return fail(HH_ERR_INVALID_ARG, "view %zu: image pointer is NULL", v);
     const uint64_t f = p->next_frame;
     PipeSlot& s = p->slot[f % kSlots];
-    cudaSetDevice(p->device);
+    const DeviceScope on(p->device);
     if (s.frame >= 0) {  // the slot's previous frame must be done with its buffers
         const cudaError_t q = wait_event(s.downloaded, kSubmitWaitMs);
         if (q == cudaErrorNotReady)
@@ -225,6 +238,7 @@ hh_status hh_pipeline_wait(hh_pipeline p, uint64_t frame, int timeout_ms) {
                     static_cast<unsigned long long>(frame));
     const PipeSlot& s = p->slot[frame % kSlots];
     if (s.frame != static_cast<int64_t>(frame)) return hh::ok();  // the slot moved on: done
+    const DeviceScope on(p->device);
     const cudaError_t q = wait_event(s.downloaded, timeout_ms < 0 ? 0 : timeout_ms);
     if (q == cudaErrorNotReady)
         return fail(HH_ERR_TIMEOUT, "frame %llu not done after %d ms",
@@ -241,7 +255,7 @@ hh_status hh_pipeline_volume(hh_pipeline p, hh_volume* vol) {
 
 hh_status hh_pipeline_free(hh_pipeline p) {
     if (!p) return hh::ok();
-    cudaSetDevice(p->device);
+    const DeviceScope on(p->device);
     cudaError_t e = cudaSuccess;
     for (const PipeSlot& s : p->slot) {
         if (s.frame < 0) continue;
