@@ -165,9 +165,11 @@ hh_status hh_splat_density(const hh_particles* particles, const hh_grid* grid, f
 /* Gladstone-Dale + gradient (Eqs. 12-13) of a given density: dn = K_gd rho,
  * g = grad dn by central differences inside and one-sided differences on the
  * first/last voxel of each axis, stored as grid->storage. For FP16 storage
- * the per-volume scales s_n = max|dn| / 16384 and s_g = max|g| / 16384 are
- * computed on the device. Allocates the volume (cudaMalloc) and returns it in
- * *out; the computation is enqueued on `stream`. */
+ * each value is stored as the nearest half of value / s with per-volume
+ * scales s_n (for dn) and s_g (for g): the smallest powers of two with
+ * max|dn| / s_n <= 16384 and max|g| / s_g <= 16384, computed on the device.
+ * Allocates the volume (cudaMalloc) and returns it in *out; the computation
+ * is enqueued on `stream`. */
 hh_status hh_volume_from_density(const float* rho_dev, const hh_grid* grid, float K_gd,
                                  void* stream, hh_volume* out);
 

@@ -4,8 +4,10 @@
 // last voxel of each axis. Packed per voxel as {dn, gx, gy, gz}:
 //   FP32: float4, 16 B/voxel (one pass: read rho, write the volume);
 //   FP16: four halves, 8 B/voxel, dn / s_n and g / s_g with per-volume scales
-//         s = max|.| / 16384 (pass 1 reduces the maxima, pass 2 recomputes the
-//         differences and quantises; rho is read twice, nothing else stored).
+//         s = the smallest power of two with max|.| / s <= 16384 (pass 1
+//         reduces the maxima, pass 2 recomputes the differences and quantises
+//         with exact multiplications by 1 / s; rho is read twice, nothing else
+//         stored).
 // Threads map to (x, y) columns, x fastest (a warp is 32 consecutive
 // columns), and walk 16 z slices each, so every load of rho is coalesced, the
 // z neighbours come from registers and the x/y neighbours from L1.
@@ -36,9 +38,17 @@ __device__ __forceinline__ size_t out_index(const OutLayout& L, int i, int j, in
     return (static_cast<size_t>(k) * ny + j) * nx + i;
 }
 
+// Scale of a channel group from the bit pattern of its maximum |value| m:
+// the smallest power of two s with m / s <= HH_FP16_CODE_MAX (the largest code
+// lies in (HH_FP16_CODE_MAX / 2, HH_FP16_CODE_MAX]); 1 for an all-zero group.
+// A power of two makes value / s exact, a multiplication by 1 / s.
 __device__ __forceinline__ float scale_of(unsigned bits) {
     const float m = __uint_as_float(bits);
-    return m > 0.0f ? m / HH_FP16_CODE_MAX : 1.0f;
+    if (!(m > 0.0f)) return 1.0f;
+    unsigned b = __float_as_uint(m * (1.0f / HH_FP16_CODE_MAX));  // exact: a power of two
+    if (b < 0x00800000u) return __uint_as_float(0x00800000u);    // below FLT_MIN: FLT_MIN
+    if (b & 0x007FFFFFu) b = (b & 0xFF800000u) + 0x00800000u;     // round up to a power of two
+    return __uint_as_float(b);
 }
 
 // Column variant: each thread owns one (i, j) column and walks a run of
@@ -69,6 +79,7 @@ __global__ void __launch_bounds__(256, MODE == 2 ? 5 : 8) field_column_kernel(co
         s_n = scale_of(max_bits[0]);
         s_g = scale_of(max_bits[1]);
     }
+    const float rs_n = 1.0f / s_n, rs_g = 1.0f / s_g;  // exact: powers of two
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && MODE != 1) {
         scales[0] = s_n;
         scales[1] = s_g;
@@ -105,11 +116,11 @@ __global__ void __launch_bounds__(256, MODE == 2 ? 5 : 8) field_column_kernel(co
                 mn = fmaxf(mn, fabsf(e.dn));
                 mg = fmaxf(mg, fmaxf(fabsf(e.gx), fmaxf(fabsf(e.gy), fabsf(e.gz))));
             } else {
-                ushort4 q;
-                q.x = __half_as_ushort(__float2half_rn(e.dn / s_n));
-                q.y = __half_as_ushort(__float2half_rn(e.gx / s_g));
-                q.z = __half_as_ushort(__float2half_rn(e.gy / s_g));
-                q.w = __half_as_ushort(__float2half_rn(e.gz / s_g));
+                ushort4 q;  // the nearest half of value / s (exact products: s is a power of two)
+                q.x = __half_as_ushort(__float2half_rn(e.dn * rs_n));
+                q.y = __half_as_ushort(__float2half_rn(e.gx * rs_g));
+                q.z = __half_as_ushort(__float2half_rn(e.gy * rs_g));
+                q.w = __half_as_ushort(__float2half_rn(e.gz * rs_g));
                 const uint2 w = make_uint2(static_cast<unsigned>(q.x) | (static_cast<unsigned>(q.y) << 16),
                                            static_cast<unsigned>(q.z) | (static_cast<unsigned>(q.w) << 16));
                 __stcs(static_cast<uint2*>(out) + o, w);

@@ -9,8 +9,9 @@
 
 #include "hh.h"
 
-// FP16 storage maps the largest |value| of a channel group to this code, so
-// every value down to ~3.7e-9 of the maximum is a normal half.
+// FP16 storage scales a channel group by the smallest power of two that maps
+// its largest |value| to at most this code (so to more than half of it), and
+// every value down to ~7e-9 of the maximum is a normal half.
 #define HH_FP16_CODE_MAX 16384.0f
 
 // Volume layouts.

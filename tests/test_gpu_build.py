@@ -111,19 +111,20 @@ def test_field_from_given_dn(gpu, oracle_lib):
 
 
 def test_field_fp16_quantisation(gpu, oracle_lib):
-    """FP16 storage: s = max|.| / 16384 per channel group; every stored value
-    is the nearest half of value / s (error <= 2^-11 relative for normal
-    halves, 2^-25 s absolute in the subnormal range)."""
+    """FP16 storage: per channel group s = the smallest power of two with
+    max|.| / s <= 16384; every stored value is the nearest half of value / s
+    (error <= 2^-11 relative for normal halves, 2^-25 s absolute in the
+    subnormal range)."""
     hh, torch = gpu
     parts = hi.plume_particles(8000, 48)
     rho = oracle_lib.splat(parts, (48, 48, 48), 2.0)
     K = float(np.float32(hi.K_GD))
     want = oracle_lib.index_field(rho.astype(np.float32).astype(np.float64), K)
     got, info = _field_gpu(hh, torch, rho, K, "fp16")
-    s_n = np.abs(want[..., 0]).max() / 16384
-    s_g = np.abs(want[..., 1:]).max() / 16384
-    assert info["s_n"] == pytest.approx(s_n, rel=1e-6)
-    assert info["s_g"] == pytest.approx(s_g, rel=1e-6)
+    s_n, s_g = info["s_n"], info["s_g"]
+    for s, m in ((s_n, np.abs(want[..., 0]).max()), (s_g, np.abs(want[..., 1:]).max())):
+        assert np.frexp(s)[0] == 0.5  # a power of two
+        assert 8192 * (1 - 1e-6) < m / s <= 16384 * (1 + 1e-6)
     assert info["scales"] == (info["s_n"], info["s_g"])
     assert info["bytes"] == 8 * 8 * 25**3  # 48 voxels + halo = 50 = 25 bricks per axis
     m = np.abs(want[..., 0]).max()
