@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -107,10 +108,56 @@ hh_status new_volume(const hh_grid* g, hh_volume* out) {
 void drop_volume(hh_volume v) {
     if (!v) return;
     cudaFree(v->rho_dev);
+    cudaFree(v->sorted_dev);
+    cudaFree(v->bins_dev);
     cudaFree(v->data);
     cudaFree(v->scales_dev);
     cudaFree(v->max_dev);
     delete v;
+}
+
+// Whether hh_volume_rebuild sorts the particles by cell before the splat:
+// when the density grid is larger than the device's L2 (so randomly ordered
+// reductions would miss it) and there are enough particles to pay for the
+// sort. HH_SPLAT_SORT=0 / 1 forces it off / on.
+bool sort_particles(const hh_volume_s* v, int64_t n) {
+    if (n <= 0 || n >= (int64_t(1) << 31)) return false;
+    const char* env = std::getenv("HH_SPLAT_SORT");
+    if (env && env[0] == '0') return false;
+    if (env && env[0] == '1') return true;
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, v->device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const size_t rho_bytes = static_cast<size_t>(v->nx) * v->ny * v->nz * sizeof(float);
+    return n >= 65536 && rho_bytes > static_cast<size_t>(l2);
+}
+
+// Grows the binning scratch of `v` to n particles (cudaMalloc, synchronous).
+hh_status sort_scratch(hh_volume_s* v, int64_t n) {
+    if (!v->bins_dev) {
+        v->n_bins = splat_bin_count(v->nx, v->ny, v->nz);
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&v->bins_dev),
+                                   2 * static_cast<size_t>(v->n_bins) * sizeof(unsigned));
+        if (e != cudaSuccess) {
+            v->bins_dev = nullptr;
+            return cuda_fail(e, "particle binning scratch");
+        }
+    }
+    if (v->sorted_cap < n) {
+        cudaFree(v->sorted_dev);
+        v->sorted_dev = nullptr;
+        v->sorted_cap = 0;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&v->sorted_dev),
+                                   static_cast<size_t>(n) * sizeof(float4));
+        if (e != cudaSuccess) {
+            v->sorted_dev = nullptr;
+            return cuda_fail(e, "sorted particle scratch");
+        }
+        v->sorted_cap = n;
+    }
+    return HH_OK;
 }
 
 hh_status volume_from(const float* rho_dev, const hh_grid* grid, float K, cudaStream_t s,
@@ -265,8 +312,16 @@ hh_status hh_volume_rebuild(hh_volume vol, const hh_particles* particles, float 
         }
     }
     cudaStream_t s = as_stream(stream);
-    cudaError_t e = launch_splat(reinterpret_cast<const float4*>(particles->xyzm_dev), particles->n,
-                                 vol->nx, vol->ny, vol->nz, vol->h_kernel, vol->rho_dev, s);
+    const float4* src = reinterpret_cast<const float4*>(particles->xyzm_dev);
+    if (sort_particles(vol, particles->n)) {
+        if ((st = sort_scratch(vol, particles->n)) != HH_OK) return st;
+        cudaError_t e = launch_bin_particles(src, particles->n, vol->nx, vol->ny, vol->nz,
+                                             vol->bins_dev, vol->sorted_dev, s);
+        if (e != cudaSuccess) return cuda_fail(e, "particle binning launch");
+        src = vol->sorted_dev;
+    }
+    cudaError_t e = launch_splat(src, particles->n, vol->nx, vol->ny, vol->nz, vol->h_kernel,
+                                 vol->rho_dev, s);
     if (e != cudaSuccess) return cuda_fail(e, "splat launch");
     e = launch_field(vol->rho_dev, vol->nx, vol->ny, vol->nz, K_gd, vol, s);
     if (e != cudaSuccess) return cuda_fail(e, "field kernel launch");

@@ -53,6 +53,10 @@ struct hh_volume_s {
     float* scales_dev;  // [2] = {s_n, s_g} on the device (1, 1 for FP32)
     unsigned* max_dev;  // [2] = bit patterns of max|dn|, max|g| (FP16 build)
     float* rho_dev;     // density scratch for particle builds (nullable)
+    float4* sorted_dev; // particles binned by cell, for grids larger than L2 (nullable)
+    int64_t sorted_cap; // particles sorted_dev holds
+    unsigned* bins_dev; // 2 x bin count counters of the binning (nullable)
+    int n_bins;         // bins of bins_dev
     int device;
 };
 
@@ -76,6 +80,14 @@ hh_status check_background(const hh_background* bg);
 // Kernel launchers. Each returns the launch status (cudaGetLastError()).
 cudaError_t launch_splat(const float4* xyzm, int64_t n, int nx, int ny, int nz, float h,
                          float* rho, cudaStream_t s);
+
+// Counting sort of particles by cubic cell (splat_bin_count bins, x-fastest)
+// into `sorted` (n float4), using `bins` (2 x splat_bin_count unsigned) as
+// counters; the splat of the sorted copy keeps its reductions within a few
+// cells at a time.
+int splat_bin_count(int nx, int ny, int nz);
+cudaError_t launch_bin_particles(const float4* xyzm, int64_t n, int nx, int ny, int nz,
+                                 unsigned* bins, float4* sorted, cudaStream_t s);
 
 cudaError_t launch_field(const float* rho, int nx, int ny, int nz, float K, hh_volume_s* vol,
                          cudaStream_t s);

@@ -17,6 +17,8 @@
 // voxels). The kernel is evaluated in r with the particle's mass folded into
 // its coefficients, and a column of exactly 8 voxels (every interior
 // particle when h = 2) is walked fully unrolled.
+#include <algorithm>
+
 #include "hh_internal.h"
 
 namespace hh {
@@ -121,7 +123,110 @@ __global__ void __launch_bounds__(256) splat_warp_kernel(const float4* __restric
     }
 }
 
+// Binning for the splat of grids larger than L2. Particles arrive in any
+// order; splatted in that order, concurrent warps scatter their reductions
+// over the whole density grid, and once the grid outgrows L2 most of them
+// miss it. Sorted by cell (a counting sort: count, one-block exclusive scan,
+// scatter with per-bin cursors), the warps in flight cover a few cells and
+// the reductions stay in L2. A cell is at least 16 voxels wide and at most
+// 64 cells span an axis (at most 2^18 cells).
+struct BinGeom {
+    int nbx, nby, nbz;
+    float inv;  // 1 / cell width
+};
+
+__host__ __device__ inline BinGeom bin_geom(int nx, int ny, int nz) {
+    const int m = nx > ny ? (nx > nz ? nx : nz) : (ny > nz ? ny : nz);
+    int w = (m + 63) / 64;
+    if (w < 16) w = 16;
+    BinGeom g;
+    g.nbx = (nx + w - 1) / w;
+    g.nby = (ny + w - 1) / w;
+    g.nbz = (nz + w - 1) / w;
+    g.inv = 1.0f / static_cast<float>(w);
+    return g;
+}
+
+// Cell of a particle; positions outside the grid (and NaN, which converts to
+// 0) go to the nearest edge cell: the order is all that matters.
+__device__ __forceinline__ int bin_of(const float4& p, const BinGeom& g) {
+    const int bx = min(max(__float2int_rd(p.x * g.inv), 0), g.nbx - 1);
+    const int by = min(max(__float2int_rd(p.y * g.inv), 0), g.nby - 1);
+    const int bz = min(max(__float2int_rd(p.z * g.inv), 0), g.nbz - 1);
+    return (bz * g.nby + by) * g.nbx + bx;
+}
+
+__global__ void bin_count_kernel(const float4* __restrict__ parts, int64_t n, BinGeom g,
+                                 unsigned* __restrict__ count) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        atomicAdd(count + bin_of(__ldg(parts + i), g), 1u);
+}
+
+// Exclusive prefix sum of count[0..nb) into offset[0..nb), one block of 1024
+// threads, each owning a contiguous chunk.
+__global__ void __launch_bounds__(1024) bin_scan_kernel(const unsigned* __restrict__ count,
+                                                        unsigned* __restrict__ offset, int nb) {
+    __shared__ unsigned warp_sum[32];
+    const int t = threadIdx.x, chunk = (nb + 1023) / 1024;
+    const int b0 = min(t * chunk, nb), b1 = min(b0 + chunk, nb);
+    unsigned sum = 0;
+    for (int b = b0; b < b1; ++b) sum += count[b];
+    // inclusive scan of the per-thread sums across the block
+    unsigned x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if ((t & 31) >= o) x += y;
+    }
+    if ((t & 31) == 31) warp_sum[t >> 5] = x;
+    __syncthreads();
+    if (t < 32) {
+        unsigned w = warp_sum[t];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+            if (t >= o) w += y;
+        }
+        warp_sum[t] = w;
+    }
+    __syncthreads();
+    unsigned run = x - sum + ((t >> 5) ? warp_sum[(t >> 5) - 1] : 0u);  // exclusive
+    for (int b = b0; b < b1; ++b) {
+        offset[b] = run;
+        run += count[b];
+    }
+}
+
+__global__ void bin_scatter_kernel(const float4* __restrict__ parts, int64_t n, BinGeom g,
+                                   unsigned* __restrict__ cursor, float4* __restrict__ sorted) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float4 p = __ldg(parts + i);
+        sorted[atomicAdd(cursor + bin_of(p, g), 1u)] = p;
+    }
+}
+
 }  // namespace
+
+int splat_bin_count(int nx, int ny, int nz) {
+    const BinGeom g = bin_geom(nx, ny, nz);
+    return g.nbx * g.nby * g.nbz;
+}
+
+cudaError_t launch_bin_particles(const float4* xyzm, int64_t n, int nx, int ny, int nz,
+                                 unsigned* bins, float4* sorted, cudaStream_t s) {
+    const BinGeom g = bin_geom(nx, ny, nz);
+    const int nb = g.nbx * g.nby * g.nbz;
+    cudaError_t e = cudaMemsetAsync(bins, 0, static_cast<size_t>(nb) * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((n + threads - 1) / threads,
+                                                                    152 * 16));
+    bin_count_kernel<<<blocks, threads, 0, s>>>(xyzm, n, g, bins);
+    bin_scan_kernel<<<1, 1024, 0, s>>>(bins, bins + nb, nb);
+    bin_scatter_kernel<<<blocks, threads, 0, s>>>(xyzm, n, g, bins + nb, sorted);
+    count_launch(3);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_splat(const float4* xyzm, int64_t n, int nx, int ny, int nz, float h,
                          float* rho, cudaStream_t s) {

@@ -274,3 +274,22 @@ def test_fullsize_serve_384_fp16(gpu, oracle_lib):
     st = assert_parity_conditioned(first, ref, oracle_lib, {"kind": "grid", "vol4": vol4}, dims,
                                    cams[0], params, sel=pix)
     assert st["hits"] >= 100
+
+
+def test_fullsize_build_384_binned(gpu, oracle_lib):
+    """The serving configuration's build at full size: 1,048,576 plume
+    particles on 384^3, whose 226 MB density grid is larger than L2, so the
+    particles are binned by cell before the splat; the FP32 volume against the
+    oracle's splat and Eqs. 12-13 on every voxel."""
+    hh, torch = gpu
+    L3 = 384
+    dims = (L3, L3, L3)
+    parts = hi.drifting_plume_frame(hi.plume_particles(1048576, L3), 5, L=L3)
+    K = float(np.float32(hi.K_GD))
+    vol = hh.hh_build_index_field(torch.from_numpy(parts).cuda(), hh.make_grid(dims, 2.0), K)
+    got = export_volume(hh, torch, vol, dims)
+    vol.close()
+    want = oracle_lib.index_field(oracle_lib.splat(parts, dims, 2.0), K)
+    m = np.abs(want[..., 0]).max()
+    assert np.abs(got[..., 0] - want[..., 0]).max() <= 2e-5 * m
+    assert np.abs(got[..., 1:] - want[..., 1:]).max() <= 2e-5 * m
