@@ -155,15 +155,16 @@ def test_build_index_field_matches_parts(gpu, oracle_lib):
 
 
 
-def test_build_with_particles_binned_by_cell(gpu, oracle_lib, monkeypatch):
+@pytest.mark.parametrize("dims,n", [((70, 37, 53), 70000),
+                                    ((1100, 20, 24), 40000)])  # 18-voxel cells: 64 along x
+def test_build_with_particles_binned_by_cell(gpu, oracle_lib, monkeypatch, dims, n):
     """hh_volume_rebuild sorts the particles by cell before the splat when the
-    density grid is larger than L2; forced here on a small ragged grid (many
+    density grid is larger than L2; forced here on small ragged grids (many
     cells, particles in random order, some outside the grid, NaN and inf):
     the volume equals the oracle's Eqs. 12-13 on its splat, as without."""
     hh, torch = gpu
     monkeypatch.setenv("HH_SPLAT_SORT", "1")
-    dims = (70, 37, 53)
-    parts = hi.random_particles(70000, dims, seed=3, margin=-3.0)
+    parts = hi.random_particles(n, dims, seed=3, margin=-3.0)
     bad = np.array([[np.nan, 5, 5, 1], [5, np.inf, 5, 1], [-np.inf, 5, 5, 1]], dtype=np.float32)
     K = float(np.float32(hi.K_GD))
     vol = hh.hh_build_index_field(torch.from_numpy(np.concatenate([parts, bad])).cuda(),
