@@ -188,8 +188,14 @@ hh_status hh_build_index_field(const hh_particles* particles, const hh_grid* gri
  * simulation frame): splat into the volume's density scratch, then Eqs.
  * 12-13, with the volume's grid, h and storage. Allocates nothing when the
  * volume came from hh_build_index_field; otherwise its first call allocates
- * the density scratch (cudaMalloc). Work queued earlier on other streams that
- * still reads the volume must be ordered before this call by the caller. */
+ * the density scratch (cudaMalloc). When the density grid is larger than the
+ * device's L2 cache, the particles are first sorted by cell into a
+ * volume-owned copy (allocated on first use, and again when the particle
+ * count grows: 16 B per particle plus 8 B per cell) so that the splat's
+ * reductions stay in L2; the environment variable HH_SPLAT_SORT=0 or 1
+ * forces this off or on. The result does not depend on it beyond the order
+ * of the FP32 atomic sums. Work queued earlier on other streams that still
+ * reads the volume must be ordered before this call by the caller. */
 hh_status hh_volume_rebuild(hh_volume vol, const hh_particles* particles, float K_gd,
                             void* stream);
 
