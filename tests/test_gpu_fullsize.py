@@ -271,9 +271,15 @@ def test_fullsize_serve_384_fp16(gpu, oracle_lib):
         v.close()
     pix = _sample_pixels(cams[0], 400, seed=500, flags=first["flags"])
     ref = oracle_lib.trace_grid(vol4, cams[0], params, bg, pixels=pix, nthreads=16)
-    st = assert_parity_conditioned(first, ref, oracle_lib, {"kind": "grid", "vol4": vol4}, dims,
-                                   cams[0], params, sel=pix)
+    field = {"kind": "grid", "vol4": vol4}
+    # rays 1.5 times as long as at 256^3: as at 512^3, no more rays are excused
+    # than the oracle alone finds ill conditioned in the sample
+    st = assert_parity_conditioned(first, ref, oracle_lib, field, dims, cams[0], params, sel=pix,
+                                   max_ill_frac=1.0)
     assert st["hits"] >= 100
+    hit_pix = pix[(ref["flags"] & 1) != 0]
+    pop_ill = int(ill_conditioned(oracle_lib, field, dims, cams[0], params, hit_pix)[0].sum())
+    assert st["n_ill"] <= pop_ill + 2
 
 
 def test_fullsize_build_384_binned(gpu, oracle_lib):
