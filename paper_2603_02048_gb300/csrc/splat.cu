@@ -164,14 +164,29 @@ __global__ void bin_count_kernel(const float4* __restrict__ parts, int64_t n, Bi
 }
 
 // Exclusive prefix sum of count[0..nb) into offset[0..nb), one block of 1024
-// threads, each owning a contiguous chunk.
+// threads, each owning a contiguous chunk (a multiple of 4 counters). When
+// nb is a multiple of 4 and a chunk at most 32, a thread holds its chunk in
+// registers, loaded and stored as 16-byte vectors; otherwise it walks it.
 __global__ void __launch_bounds__(1024) bin_scan_kernel(const unsigned* __restrict__ count,
                                                         unsigned* __restrict__ offset, int nb) {
     __shared__ unsigned warp_sum[32];
-    const int t = threadIdx.x, chunk = (nb + 1023) / 1024;
+    constexpr int kVec = 8;  // 16-byte vectors a thread holds
+    const int t = threadIdx.x;
+    const int chunk = (((nb + 1023) / 1024) + 3) & ~3;
+    const bool vec = (nb & 3) == 0 && chunk <= 4 * kVec;
     const int b0 = min(t * chunk, nb), b1 = min(b0 + chunk, nb);
+    uint4 v[kVec];
     unsigned sum = 0;
-    for (int b = b0; b < b1; ++b) sum += count[b];
+    if (vec) {
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            v[j] = b0 + 4 * j < b1 ? reinterpret_cast<const uint4*>(count + b0)[j]
+                                   : make_uint4(0u, 0u, 0u, 0u);
+            sum += v[j].x + v[j].y + v[j].z + v[j].w;
+        }
+    } else {
+        for (int b = b0; b < b1; ++b) sum += count[b];
+    }
     // inclusive scan of the per-thread sums across the block
     unsigned x = sum;
     for (int o = 1; o < 32; o <<= 1) {
@@ -190,9 +205,24 @@ __global__ void __launch_bounds__(1024) bin_scan_kernel(const unsigned* __restri
     }
     __syncthreads();
     unsigned run = x - sum + ((t >> 5) ? warp_sum[(t >> 5) - 1] : 0u);  // exclusive
-    for (int b = b0; b < b1; ++b) {
-        offset[b] = run;
-        run += count[b];
+    if (vec) {
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            if (b0 + 4 * j < b1) {
+                uint4 o;
+                o.x = run;
+                o.y = o.x + v[j].x;
+                o.z = o.y + v[j].y;
+                o.w = o.z + v[j].z;
+                run = o.w + v[j].w;
+                reinterpret_cast<uint4*>(offset + b0)[j] = o;
+            }
+        }
+    } else {
+        for (int b = b0; b < b1; ++b) {
+            offset[b] = run;
+            run += count[b];
+        }
     }
 }
 

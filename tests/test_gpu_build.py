@@ -155,8 +155,9 @@ def test_build_index_field_matches_parts(gpu, oracle_lib):
 
 
 
-@pytest.mark.parametrize("dims,n", [((70, 37, 53), 70000),
-                                    ((1100, 20, 24), 40000)])  # 18-voxel cells: 64 along x
+@pytest.mark.parametrize("dims,n", [((70, 37, 53), 70000),    # 60 cells
+                                    ((1100, 20, 24), 40000),   # 18-voxel cells: 64 along x
+                                    ((33, 33, 33), 20000)])    # 27 cells: the scan's scalar path
 def test_build_with_particles_binned_by_cell(gpu, oracle_lib, monkeypatch, dims, n):
     """hh_volume_rebuild sorts the particles by cell before the splat when the
     density grid is larger than L2; forced here on small ragged grids (many
