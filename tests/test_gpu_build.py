@@ -178,3 +178,81 @@ def test_build_with_particles_binned_by_cell(gpu, oracle_lib, monkeypatch, dims,
     m = np.abs(want[..., 0]).max()
     assert np.abs(got[..., 0] - want[..., 0]).max() <= 2e-5 * m
     assert np.abs(got[..., 1:] - want[..., 1:]).max() <= 2e-5 * m
+
+
+@pytest.mark.parametrize("path", ["trace", "batch", "graph", "none"])
+def test_rebuild_after_marches_equals_a_fresh_build(gpu, path):
+    """Rebuild / march cycles on one volume and one stream (marches through
+    hh_trace, a batched launch or its graph, or none): a rebuild from particle
+    set B after rebuilds from set A equals a fresh build from B (up to the
+    order of the FP32 atomic sums), so nothing of an earlier frame's density
+    survives."""
+    hh, torch = gpu
+    from parity_util import export_volume
+
+    dims = (40, 36, 44)
+    K = float(np.float32(hi.K_GD))
+    pa = torch.from_numpy(hi.plume_particles(6000, 36, seed=21)).cuda()
+    pb = torch.from_numpy(hi.plume_particles(5000, 36, seed=22)).cuda()
+    cams = [hi.orbit_camera(dims, 30.0, 10.0, 32, 24)]
+    params = hi.params_euler_adaptive(dims, theta_max=1e-5)
+    bg = torch.from_numpy(hi.checker_background()).cuda()
+    outs = [{"rgb": torch.empty(32 * 24 * 3, device="cuda")}]
+    fresh = hh.hh_build_index_field(pb, hh.make_grid(dims, 2.0), K)
+    want = export_volume(hh, torch, fresh, dims)
+    fresh.close()
+    vol = hh.hh_build_index_field(pa, hh.make_grid(dims, 2.0), K)
+    batch = hh.hh_batch_create(vol, cams, params, bg, outs) if path in ("batch", "graph") else None
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for rep in range(2):
+            hh.hh_volume_rebuild(vol, pa, K, s)
+            if path == "trace":
+                hh.hh_trace(vol, cams, params, bg, outs, s)
+                hh.hh_trace(vol, cams, params, bg, outs, s)  # a second march: nothing left to clear
+            elif path == "batch":
+                hh.hh_batch_launch(batch, s)
+            elif path == "graph":
+                hh.hh_batch_launch_graph(batch, s)
+                hh.hh_batch_launch_graph(batch, s)
+        hh.hh_volume_rebuild(vol, pb, K, s)
+    torch.cuda.synchronize()
+    got = export_volume(hh, torch, vol, dims)
+    m = np.abs(want[..., 0]).max()
+    assert np.abs(got - want).max() <= 1e-5 * m
+    if batch is not None:
+        batch.close()
+    vol.close()
+
+
+def test_rebuild_of_a_volume_built_from_a_density(gpu):
+    """A volume built from a given density has no density scratch of its own;
+    its first rebuild from particles allocates one, and later rebuilds reuse
+    it, with a batched graph replayed in between: each equals a fresh build."""
+    hh, torch = gpu
+    from parity_util import export_volume
+
+    dims = (24, 20, 28)
+    K = float(np.float32(hi.K_GD))
+    rho = torch.zeros(24 * 20 * 28, device="cuda")
+    vol = hh.hh_volume_from_density(rho, hh.make_grid(dims, 2.0), K)
+    cams = [hi.orbit_camera(dims, 0.0, 0.0, 16, 16)]
+    params = hi.params_euler_adaptive(dims, theta_max=1e-5)
+    bg = torch.from_numpy(hi.checker_background()).cuda()
+    outs = [{"rgb": torch.empty(16 * 16 * 3, device="cuda")}]
+    batch = hh.hh_batch_create(vol, cams, params, bg, outs)
+    s = torch.cuda.Stream()
+    parts = torch.from_numpy(hi.plume_particles(3000, 20, seed=5)).cuda()
+    with torch.cuda.stream(s):
+        hh.hh_batch_launch_graph(batch, s)
+        for _ in range(2):
+            hh.hh_volume_rebuild(vol, parts, K, s)
+            hh.hh_batch_launch_graph(batch, s)
+    torch.cuda.synchronize()
+    got = export_volume(hh, torch, vol, dims)
+    fresh = hh.hh_build_index_field(parts, hh.make_grid(dims, 2.0), K)
+    want = export_volume(hh, torch, fresh, dims)
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want[..., 0]).max()
+    batch.close()
+    fresh.close()
+    vol.close()
