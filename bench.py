@@ -6,19 +6,22 @@ onto a 256^3 grid (Sec. 3.3.1), Gladstone-Dale + gradient into the FP32
 1920x1080 view (Eqs. 14-18) with the background lookup.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload frame|precision|batch]
+                    [--workload frame|precision|batch|serve]
 
 --workload precision / batch time the FP16 multi-view configurations (8 views
 of 1280x720 on the 256^3 scene; 32 uneven views on a 512^3 volume from
 2,097,152 particles) through the persistent batched launch, and add the same
-views' per-view and plain FP32 single-view march rates for comparison.
+views' per-view and plain FP32 single-view march rates for comparison;
+--workload serve drives the render server with Poisson request streams.
 
 Prints one JSON line. `value` is Mrays/s of whole steps (primary rays over
 the device time of splat + field + march, inputs resident in HBM, L2 flushed
-between timed steps); `e2e` is the same through the C ABI with the particles
-copied from pinned host memory and the image copied back inside the timed
-region. `--impl reference` times the FP64 CPU oracle on a bounded sample of
-the same workload. N > 1 (torchrun) runs independent replicas, one per GPU.
+between timed steps); `e2e` is the same end to end through the C ABI with
+host buffers (the frame pipeline: particles from pinned host memory in, every
+view's RGB8 image back, two frames in flight), with the one-frame-at-a-time
+measurement beside it. `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload. N > 1 (torchrun) runs independent
+replicas, one per GPU.
 """
 from __future__ import annotations
 
