@@ -1,6 +1,9 @@
 // C ABI of the curved-ray heat-haze engine (declared in include/hh.h):
-// argument validation, volume handles, stream-ordered scratch and error
-// reporting around the kernels of splat.cu, field.cu and march.cu.
+// argument validation, volume handles, stream-ordered scratch (the density
+// grid, and for grids larger than L2 the particles binned by cell) and error
+// reporting around the kernels of splat.cu, field.cu and march.cu. The batch
+// API lives with its kernel in march.cu, the frame pipeline in pipeline.cpp,
+// the render server in serve.cpp.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
