@@ -56,8 +56,10 @@ __device__ __forceinline__ float scale_of(unsigned bits) {
 // from memory about once per voxel plus the four x/y neighbours (L1 hits).
 #define FIELD_ZRUN 16
 
+// 8 resident blocks of 256 threads for every mode (32 registers); the FP16
+// store pass with 5 (48 registers) was 6-8 % slower.
 template <int MODE>  // 0: FP32 store, 1: FP16 max pass, 2: FP16 store
-__global__ void __launch_bounds__(256, MODE == 2 ? 5 : 8) field_column_kernel(const float* __restrict__ rho, int nx,
+__global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __restrict__ rho, int nx,
                                                            int ny, int nz, float K, OutLayout L,
                                                            void* __restrict__ out,
                                                            unsigned* __restrict__ max_bits,
