@@ -173,7 +173,8 @@ hh_status hh_splat_density(const hh_particles* particles, const hh_grid* grid, f
 hh_status hh_volume_from_density(const float* rho_dev, const hh_grid* grid, float K_gd,
                                  void* stream, hh_volume* out);
 
-/* Same with dn given directly (equivalent to K_gd = 1 on rho = dn). */
+/* Same with dn given directly: Eq. 12's dn supplied, Eq. 13's gradient
+ * computed (equivalent to K_gd = 1 on rho = dn). */
 hh_status hh_volume_from_dn(const float* dn_dev, const hh_grid* grid, void* stream,
                             hh_volume* out);
 
@@ -204,7 +205,8 @@ hh_status hh_volume_rebuild(hh_volume vol, const hh_particles* particles, float 
  * owns the whole device-memory budget and forbids libraries from allocating,
  * or a real-time frame loop that must not pay cudaMalloc's implicit device
  * synchronisation and unbounded latency). Same computation as
- * hh_build_index_field with FP32 storage, but the density grid lives in a
+ * hh_build_index_field (Sec. 3.3.1, Eqs. 12-13) with FP32 storage, but the
+ * density grid lives in a
  * fixed device array compiled into the library (8 MiB, held on every device
  * that loads the library until the process exits) and the result is written
  * to the caller's vol4_dev: nx*ny*nz*4 floats {dn, gx, gy, gz} per voxel,
@@ -221,20 +223,24 @@ hh_status hh_volume_rebuild(hh_volume vol, const hh_particles* particles, float 
 hh_status hh_build_index_field_noalloc(const hh_particles* particles, const hh_grid* grid,
                                        float K_gd, float* vol4_dev, void* stream);
 
-/* Writes the volume as the march reads it, dequantised to FP32, into dst_dev:
- * nx*ny*nz*4 floats {dn, gx, gy, gz} per voxel (x fastest). */
+/* Writes the volume as the march reads it (the {dn, grad n} field of Eqs.
+ * 12-13 that Sec. 3.3.1's trilinear sampling reads), dequantised to FP32,
+ * into dst_dev: nx*ny*nz*4 floats {dn, gx, gy, gz} per voxel (x fastest). */
 hh_status hh_volume_export(hh_volume vol, float* dst_dev, void* stream);
 
-/* Grid, FP16 scales (1 for FP32 storage) and device bytes of a volume.
- * Synchronises `stream` to read the scales. Any output may be NULL. */
+/* Grid, FP16 scales (1 for FP32 storage) and device bytes of a volume
+ * (bookkeeping; no paper passage). Synchronises `stream` to read the scales.
+ * Any output may be NULL. */
 hh_status hh_volume_info(hh_volume vol, hh_grid* grid, float* s_n, float* s_g, size_t* bytes,
                          void* stream);
 
-/* The FP16 scales alone (1, 1 for FP32 storage): hh_volume_info on the
- * legacy default stream. Synchronises it; either output may be NULL. */
+/* The FP16 scales alone (1, 1 for FP32 storage; bookkeeping, no paper
+ * passage): hh_volume_info on the legacy default stream. Synchronises it;
+ * either output may be NULL. */
 hh_status hh_volume_scales(hh_volume vol, float* s_n, float* s_g);
 
-/* Releases the volume (cudaFree; synchronises the device first). NULL is ok. */
+/* Releases the volume (cudaFree; synchronises the device first). NULL is ok.
+ * Bookkeeping; no paper passage. */
 hh_status hh_volume_free(hh_volume vol);
 
 /* ---------------------------------------------------------------------- */
@@ -276,8 +282,9 @@ typedef struct {
     int tile_w;        /* pixel tile of a warp: tile_w x (32 / tile_w), 4/8/16 */
 } hh_batch_config;
 
-/* Creates a batch of n_cams views (1..4096) over `vol`; outs[i] belongs to
- * cams[i] (same layout and rules as hh_trace). The library copies the view
+/* Creates a batch of n_cams views (1..4096) over `vol` (the multi-camera
+ * rendering of Sec. 4.1); outs[i] belongs to cams[i] (same layout and rules
+ * as hh_trace). The library copies the view
  * table to the device (cudaMalloc + synchronous copy); the volume, the
  * background and the output buffers stay owned by the caller and must
  * outlive the batch. Default configuration: {128, 0, 32, 8}. */
@@ -285,12 +292,16 @@ hh_status hh_batch_create(hh_volume vol, const hh_camera* cams, int n_cams,
                           const hh_step_params* params, const hh_background* bg,
                           const hh_view_out* outs, hh_batch* out);
 
-/* Sets / reads the launch shape. Setting a new tile_w re-uploads the view
- * table (synchronous). Get reports blocks_per_sm resolved to a number. */
+/* Sets / reads the launch shape (a GPU scheduling choice; no paper passage).
+ * Setting a new tile_w re-uploads the view table (synchronous). Get reports
+ * blocks_per_sm resolved to a number. Both return HH_ERR_INVALID_ARG for a
+ * NULL batch or config, set also for a shape outside the ranges above. */
 hh_status hh_batch_set_config(hh_batch b, const hh_batch_config* cfg);
+/* (The read half of the pair above.) */
 hh_status hh_batch_get_config(hh_batch b, hh_batch_config* cfg);
 
-/* Times candidate configurations (tile 8x4 / 4x8 / 16x2; 64, 128, 256 threads;
+/* Autotuner (a GPU scheduling search; no paper passage). Times candidate
+ * configurations (tile 8x4 / 4x8 / 16x2; 64, 128, 256 threads;
  * compaction at 32, 16, 8 idle lanes; full or half occupancy) with CUDA events
  * on `stream`, each as the median of |reps| launches, and keeps the fastest.
  * Results are cached in the process by workload (grid, storage, schedule,
@@ -299,15 +310,18 @@ hh_status hh_batch_get_config(hh_batch b, hh_batch_config* cfg);
 hh_status hh_batch_autotune(hh_batch b, int reps, void* stream, hh_batch_config* best);
 
 /* Enqueues one persistent launch (a counter reset plus one kernel) on
- * `stream`; it can be captured into a CUDA graph by the caller. */
+ * `stream`: every view's march of Secs. 3.3.2-3.3.3, as hh_trace computes it.
+ * It can be captured into a CUDA graph by the caller. */
 hh_status hh_batch_launch(hh_batch b, void* stream);
 
-/* Same launch through a CUDA graph the batch captures on its first call (on
+/* Same launch (Secs. 3.3.2-3.3.3 for every view) through a CUDA graph the
+ * batch captures on its first call (on
  * `stream`, which must be a created stream, not the legacy default) and
  * replays afterwards. A new configuration or stream re-captures. */
 hh_status hh_batch_launch_graph(hh_batch b, void* stream);
 
-/* Releases the batch (its graph, view table and counter). NULL is ok. */
+/* Releases the batch (its graph, view table and counter). NULL is ok.
+ * Bookkeeping; no paper passage. */
 hh_status hh_batch_free(hh_batch b);
 
 /* ---------------------------------------------------------------------- */
@@ -324,7 +338,8 @@ hh_status hh_batch_free(hh_batch b);
  * overlap the kernels. One thread drives a pipeline. */
 typedef struct hh_pipeline_s* hh_pipeline;
 
-/* Creates a pipeline for the views cams[0..n_cams) (1..4096) of a volume on
+/* Creates a pipeline (the Sec. 3.3 frame loop above) for the views
+ * cams[0..n_cams) (1..4096) of a volume on
  * `grid` (h_kernel > 0) with Gladstone-Dale constant K_gd, for up to
  * max_particles particles per frame. cfg NULL: one hh_trace launch per view;
  * otherwise the views run as one batched launch (hh_batch, bit-identical to
@@ -338,7 +353,8 @@ hh_status hh_pipeline_create(const hh_grid* grid, float K_gd, int64_t max_partic
                              const hh_background* bg, const hh_batch_config* cfg,
                              hh_pipeline* out);
 
-/* Enqueues frame t (its number, counting from 0, in *frame): upload of the
+/* Enqueues frame t of the Sec. 3.3 loop (its number, counting from 0, in
+ * *frame): upload of the
  * n particles (float4 {x, y, z, m} in voxel units) at xyzm_host, volume
  * rebuild (hh_volume_rebuild), the march of every view, and the download of
  * view i's H*W*3 bytes to rgb8_host[i]. Returns once the frame is enqueued;
@@ -351,17 +367,18 @@ hh_status hh_pipeline_submit(hh_pipeline p, const float* xyzm_host, int64_t n,
                              uint8_t* const* rgb8_host, uint64_t* frame);
 
 /* Waits, at most timeout_ms (HH_ERR_TIMEOUT after), until frame's images
- * are in host memory. HH_ERR_NOT_FOUND for a frame not yet submitted; a
+ * are in host memory (frame bookkeeping; no paper passage). HH_ERR_NOT_FOUND for a frame not yet submitted; a
  * frame two or more behind the last submitted one is complete. */
 hh_status hh_pipeline_wait(hh_pipeline p, uint64_t frame, int timeout_ms);
 
-/* The pipeline's volume (owned by the pipeline, valid until
+/* The pipeline's volume (bookkeeping, no paper passage; owned by the pipeline, valid until
  * hh_pipeline_free); once frame t has been waited for and no later frame
  * submitted, it holds frame t's volume. */
 hh_status hh_pipeline_volume(hh_pipeline p, hh_volume* vol);
 
 /* Waits (bounded, 60 s per frame) for the submitted frames and releases the
- * pipeline; HH_ERR_TIMEOUT leaves it allocated. NULL is ok. */
+ * pipeline; HH_ERR_TIMEOUT leaves it allocated. NULL is ok. Bookkeeping; no
+ * paper passage. */
 hh_status hh_pipeline_free(hh_pipeline p);
 
 /* ---------------------------------------------------------------------- */
@@ -394,61 +411,77 @@ typedef struct {
     size_t pool_used, pool_capacity; /* bytes of the output budget         */
 } hh_serve_stats;
 
-/* Creates a server on the current device with `mem_budget_bytes` of output
- * memory (one cudaMalloc; HH_ERR_OOM if the device cannot provide it) and
+/* Creates a server (the multi-camera serving above, Secs. 1 and 4.2) on the
+ * current device with `mem_budget_bytes` of output memory (one cudaMalloc; HH_ERR_OOM if the device cannot provide it) and
  * `max_slots` concurrent requests (1..64, one stream each). */
 hh_status hh_serve_create(size_t mem_budget_bytes, int max_slots, hh_server* out);
 
-/* Launch shape used for every request (see hh_batch_config). */
+/* Launch shape used for every request (see hh_batch_config; a GPU scheduling
+ * choice, no paper passage). HH_ERR_INVALID_ARG for a shape out of range. */
 hh_status hh_serve_set_config(hh_server s, const hh_batch_config* cfg);
 
-/* Registers the volume of simulation frame `frame_id` (the server borrows
+/* Registers the volume of simulation frame `frame_id` (the time-varying
+ * volume of Sec. 4.2; the server borrows
  * it: its build must have finished, and it must stay alive and unchanged
  * while requests on it run; the server's streams do not wait for others). Replacing
  * or removing a frame that is being rendered returns HH_ERR_BUSY. */
 hh_status hh_serve_put_volume(hh_server s, int64_t frame_id, hh_volume vol);
+/* Unregisters frame `frame_id` (bookkeeping, no paper passage; the caller
+ * keeps the volume):
+ * HH_ERR_NOT_FOUND for an unknown frame, HH_ERR_BUSY while requests on it run. */
 hh_status hh_serve_remove_volume(hh_server s, int64_t frame_id);
 
-/* Queues a request of n_views cameras on frame `frame_id`; returns its
+/* Queues a request of n_views cameras on frame `frame_id` (each view is
+ * hh_trace's march of Secs. 3.3.2-3.3.3); returns its
  * ticket at once. `outputs` is a mask of HH_OUT_* bits; without HH_OUT_RGB
  * and HH_OUT_RGB8 the float image (HH_OUT_RGB) is made. */
 hh_status hh_serve_submit(hh_server s, int64_t frame_id, const hh_camera* cams, int n_views,
                           const hh_step_params* params, const hh_background* bg, int outputs,
                           uint64_t* ticket);
 
-/* HH_OK (with the submit-to-completion latency in ms) when the request is
+/* Request status (bookkeeping; no paper passage): HH_OK (with the
+ * submit-to-completion latency in ms) when the request is
  * done, HH_ERR_BUSY while it waits or runs, HH_ERR_CANCELLED,
  * HH_ERR_NOT_FOUND for unknown or released tickets, HH_ERR_CUDA on failure. */
 hh_status hh_serve_poll(hh_server s, uint64_t ticket, double* latency_ms);
 
-/* As poll, but waits up to timeout_ms (HH_ERR_TIMEOUT when it runs out). */
+/* As poll, but waits up to timeout_ms (HH_ERR_TIMEOUT when it runs out;
+ * bookkeeping, no paper passage). */
 hh_status hh_serve_wait(hh_server s, uint64_t ticket, int timeout_ms, double* latency_ms);
 
-/* Device pointers of a done request's view outputs (inside the server's
+/* Device pointers of a done request's view outputs, the march results of
+ * Secs. 3.3.2-3.3.3 (inside the server's
  * budget; valid until hh_serve_release). Pixel layout as hh_view_out. */
 hh_status hh_serve_view(hh_server s, uint64_t ticket, int view, hh_view_out* out);
 
-/* Frees a finished request's outputs and forgets its ticket; a waiting or
+/* Frees a finished request's outputs and forgets its ticket (bookkeeping, no
+ * paper passage); a waiting or
  * running request returns HH_ERR_BUSY (cancel it first). */
 hh_status hh_serve_release(hh_server s, uint64_t ticket);
 
-/* Cancels a request: a waiting one at once, a running one when its launch
+/* Cancels a request (bookkeeping, no paper passage): a waiting one at once, a
+ * running one when its launch
  * ends (its result is discarded). Cancelled requests still need releasing. */
 hh_status hh_serve_cancel(hh_server s, uint64_t ticket);
 
+/* Counters of the server's life so far (hh_serve_stats; bookkeeping, no
+ * paper passage). HH_ERR_INVALID_ARG for a NULL server or output. */
 hh_status hh_serve_get_stats(hh_server s, hh_serve_stats* out);
 
-/* Stops the worker, waits for running launches and frees the server. */
+/* Stops the worker, waits for running launches and frees the server
+ * (bookkeeping, no paper passage). */
 hh_status hh_serve_destroy(hh_server s);
 
 /* ---------------------------------------------------------------------- */
 /* Diagnostics                                                             */
 /* ---------------------------------------------------------------------- */
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none; diagnostics,
+ * no paper passage). The pointer stays valid until the thread's next call. */
 const char* hh_last_error(void);
 
-/* Number of kernels this library has launched in this process. */
+/* Number of kernels this library has launched in this process (diagnostics,
+ * no paper passage; graph replays count one each). */
 uint64_t hh_kernel_launch_count(void);
 
 #ifdef __cplusplus
