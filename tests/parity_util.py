@@ -14,14 +14,19 @@ more than that. So every ray must meet the tolerance, except rays whose
 oracle answer itself moves by more than half the tolerance when the start
 state is perturbed at FP32 rounding scale (one ulp of the entry point, 2^-23
 rad of direction) or whose step count changes under that perturbation. Those
-ill-conditioned rays are counted, must stay rare, and their GPU result must
-lie within five times the oracle's own perturbation spread (six random
-perturbations; plus the tolerance). When the step count itself changes under
-that perturbation (the last step lands within rounding of a box face), one
-step more or less turns the exit direction by at most one step's turning
-angle, which Eq. 18 bounds by theta_max (fixed steps: h max|grad n|); that
-bound is added for those rays. The step count itself is reported, not
-judged: a ray may take one step more or less and still exit within tolerance.
+ill-conditioned rays are counted against a per-test cap (close to the rate
+measured on that workload), and their GPU result must lie within five times
+the oracle's own perturbation spread (plus the tolerance). Only a ray whose
+GPU step count differs from the oracle's by exactly one (its last step lands
+within rounding of a box face) gets one more allowance: the turn of the step
+that one side took and the other did not, read off the oracle's own path
+(the turn of its last step, or of one more step from its exit point along its
+exit direction), never a bound from theta_max. The image RMSE bound applies
+to every compared ray, excused ones included.
+
+With HH_PARITY_LOG set to a file name, every check appends one JSON line of
+its statistics (hits, rays beyond tolerance, ill-conditioned rays, the worst
+excess over the tolerance) to that file.
 """
 from __future__ import annotations
 
@@ -220,22 +225,43 @@ def ill_conditioned(oracle, field, box, cam, params, pix, n_pert=6, seed=0):
     return ill, s_dir, s_pos, s_steps
 
 
-def one_step_turn(params: dict, field) -> float:
-    """Largest turning angle of one step: a step of length h turns by at most
-    h max|grad n| / min n; Eq. 18 keeps unclamped and h_max-clamped steps
-    below theta_max, so only a step clamped at h_min can turn further."""
-    vol4 = field.get("vol4")
-    gmax = float(np.linalg.norm(vol4[..., 1:], axis=-1).max()) if vol4 is not None else 1.0
-    nmin = max(1.0 + float(vol4[..., 0].min()) if vol4 is not None else 1.0, 1e-3)
-    if params.get("adaptive"):
-        return max(float(params["theta_max"]), float(params["h_min"]) * gmax / nmin)
-    return float(params["h_fixed"]) * gmax / nmin
+def step_turns(oracle, field, box, C0, w0, params):
+    """For each ray from (C0, w0): the turn of the oracle's last step (the
+    angle between the direction before and after it) and the turn of one more
+    step from its exit point along its exit direction. They bound the
+    difference a step count one higher or one lower makes: the step that one
+    side took and the other did not, at the same place to within rounding."""
+    last = np.zeros(len(C0))
+    nxt = np.zeros(len(C0))
+    one = dict(params, max_steps=1)
+    for i in range(len(C0)):
+        m = oracle.march_ray(field, box, C0[i], w0[i], params, path_cap=int(params["max_steps"]))
+        if m["steps"] > 0:
+            last[i] = float(angle(m["path"][-1, 3:6], m["exit_dir"]))
+        q = oracle.march_ray(field, box, m["exit_pos"], m["exit_dir"], one)
+        nxt[i] = float(angle(m["exit_dir"], q["exit_dir"]))
+    return last, nxt
+
+
+def _log(st: dict, label):
+    import json
+    import os
+
+    path = os.environ.get("HH_PARITY_LOG")
+    if not path:
+        return
+    rec = {"test": label or os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0]}
+    rec.update({k: v for k, v in st.items() if isinstance(v, (int, float, bool, str))})
+    with open(path, "a") as f:
+        f.write(json.dumps(rec) + "\n")
 
 
 def assert_parity_conditioned(gpu: dict, ref: dict, oracle, field, box, cam, params, sel=None,
-                              max_ill_frac: float = 0.02) -> dict:
+                              max_ill_frac: float = 0.005, label=None) -> dict:
     """Parity with the conditioning rule above. gpu holds the whole view (or
-    `sel` picks the pixels that ref holds, in ref's order)."""
+    `sel` picks the pixels that ref holds, in ref's order). At most
+    max_ill_frac of the hit rays (plus two) may be excused as ill conditioned.
+    Returns the statistics (also appended to HH_PARITY_LOG when set)."""
     st = compare(gpu, ref, sel, box=box)
     g = {k: (v if sel is None else v[sel]) for k, v in gpu.items()}
     pix = np.arange(len(g["steps"])) if sel is None else np.asarray(sel)
@@ -249,6 +275,10 @@ def assert_parity_conditioned(gpu: dict, ref: dict, oracle, field, box, cam, par
     idx = np.flatnonzero(bad)
     st["n_bad"] = int(len(idx))
     st["n_ill"] = 0
+    st["n_turn"] = 0
+    # worst excess over the plain tolerance, as a multiple of it
+    st["worst_dir_over_tol"] = float(ang.max() / DIR_TOL) if len(ang) else 0.0
+    st["worst_pos_over_tol"] = float(pos[hit_r].max() / POS_TOL) if hit_r.any() else 0.0
     if len(idx):
         ill, s_dir, s_pos, s_steps = ill_conditioned(oracle, field, box, cam, params, pix[idx])
         if not np.all(ill):
@@ -268,20 +298,32 @@ def assert_parity_conditioned(gpu: dict, ref: dict, oracle, field, box, cam, par
                  "spread_pos": s_pos[show].tolist(), "steps_changed": s_steps[show].tolist(),
                  "ill": ill[show].tolist()}
         assert np.all(ill), dict(st, **worst)
-        turn = np.where(s_steps, one_step_turn(params, field), 0.0)
-        over = (ang[idx] > DIR_TOL + 5 * s_dir + turn) | (pos[idx] > POS_TOL + 5 * s_pos)
+        # the one-step allowance: only where the step counts differ by one
+        dk = g["steps"][idx].astype(np.int64) - ref["steps"][idx].astype(np.int64)
+        turn = np.zeros(len(idx))
+        k1 = np.flatnonzero(np.abs(dk) == 1)
+        if len(k1):
+            C0, w0 = start_states(oracle, cam, box, pix[idx][k1])
+            last, nxt = step_turns(oracle, field, box, C0, w0, params)
+            turn[k1] = np.where(dk[k1] < 0, last, nxt)
+        st["n_turn"] = int(len(k1))
+
+        def over_of():
+            return (ang[idx] > DIR_TOL + 5 * s_dir + turn) | (pos[idx] > POS_TOL + 5 * s_pos)
+
+        over = over_of()
         if over.any():
             # beyond what one rounding at the start explains: measure the
             # rounding made at every step along the ray (path_spread)
             j = np.flatnonzero(over)
             C0, w0 = start_states(oracle, cam, box, pix[idx][j])
-            p_dir, p_pos, p_steps = path_spread(oracle, field, box, C0, w0, params)
+            p_dir, p_pos, _ = path_spread(oracle, field, box, C0, w0, params)
             s_dir[j] = np.maximum(s_dir[j], p_dir)
             s_pos[j] = np.maximum(s_pos[j], p_pos)
-            s_steps[j] |= p_steps
-            turn = np.where(s_steps, one_step_turn(params, field), 0.0)
-            over = (ang[idx] > DIR_TOL + 5 * s_dir + turn) | (pos[idx] > POS_TOL + 5 * s_pos)
+            over = over_of()
             st["n_path"] = int(len(j))
+        excess = ang[idx] / (DIR_TOL + 5 * s_dir + turn)
+        st["worst_over_bound"] = float(excess.max())
         if over.any():
             k = np.flatnonzero(over)[:5]
             worst = {"over": int(over.sum()), "pixels": pix[idx][k].tolist(),
@@ -293,17 +335,32 @@ def assert_parity_conditioned(gpu: dict, ref: dict, oracle, field, box, cam, par
                      "gpu_exit": g["exit_pos"][idx][k].tolist(),
                      "oracle_exit": ref["exit_pos"][idx][k].tolist()}
         assert not over.any(), dict(st, **worst)
-    assert st["n_ill"] <= max_ill_frac * max(int(hit_r.sum()), 1) + 2, st
-    # image RMSE: over the whole view when the whole view is compared; over a
-    # sample, across the rays held to the tolerances (an excused ray's colour
-    # follows from its exit direction and position, bounded above, and in a
-    # sample of a hundred pixels one of them alone could exceed the bound)
-    if sel is None:
-        assert st["rmse"] <= RMSE_TOL, st
-    well = np.ones(len(g["rgb"]), dtype=bool)
-    well[idx] = False
-    st["rmse_held"] = (float(np.sqrt(np.mean((g["rgb"][well] - ref["rgb"][well]) ** 2)))
-                       if well.any() else 0.0)
-    assert st["rmse_held"] <= RMSE_TOL, st
+    st["max_ill"] = int(max_ill_frac * max(int(hit_r.sum()), 1)) + 2
+    _log(st, label)
+    assert st["n_ill"] <= st["max_ill"], st
+    # image RMSE over every compared ray, excused ones included
+    assert st["rmse"] <= RMSE_TOL, st
     assert np.array_equal(hit_g, hit_r)
+    return st
+
+
+def assert_parity_plain(gpu: dict, ref: dict, box, sel=None, label=None) -> dict:
+    """Parity with no excusal at all: every ray within the exit position and
+    direction tolerances with the oracle's flags, and the image RMSE bound.
+    For schedules on which the march is well conditioned everywhere (fixed
+    steps; Eq. 18 when it keeps every step at h_max)."""
+    st = compare(gpu, ref, sel, box=box)
+    g = {k: (v if sel is None else v[sel]) for k, v in gpu.items()}
+    ang = angle(g["exit_dir"], ref["exit_dir"])
+    pos = np.abs(g["exit_pos"] - ref["exit_pos"]).max(axis=1)
+    bad = (ang > DIR_TOL) | (pos > POS_TOL) | (g["flags"] != ref["flags"])
+    hit_r = (ref["flags"] & 1) != 0
+    st.update({"n_bad": int(bad.sum()), "n_ill": 0, "n_turn": 0, "max_ill": 0,
+               "worst_dir_over_tol": float(ang.max() / DIR_TOL) if len(ang) else 0.0,
+               "worst_pos_over_tol": float(pos[hit_r].max() / POS_TOL) if hit_r.any() else 0.0,
+               "rule": "plain"})
+    _log(st, label)
+    assert st["hit_mismatch"] == 0, st
+    assert st["n_bad"] == 0, dict(st, pixels=np.flatnonzero(bad)[:5].tolist())
+    assert st["rmse"] <= RMSE_TOL, st
     return st

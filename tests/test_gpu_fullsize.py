@@ -11,8 +11,8 @@ import numpy as np
 import pytest
 
 import hh_inputs as hi
-from parity_util import (angle, assert_parity_conditioned, export_volume, f32, gpu_trace,
-                         ill_conditioned)
+from parity_util import (angle, assert_parity_conditioned, assert_parity_plain, export_volume,
+                         f32, gpu_trace, ill_conditioned)
 
 pytestmark = pytest.mark.gpu
 
@@ -113,6 +113,30 @@ def test_fullsize_1080p_whole_frame(gpu, oracle_lib, scene, storage):
     assert q[0] <= 1e-7  # the typical ray is well inside the tolerance
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_fullsize_1080p_whole_frame_paper_theta_plain(gpu, oracle_lib, scene, storage):
+    """The whole 1080p frame at the paper's theta_max = 3e-3, where Eq. 18
+    keeps every step at h_max on this plume: no ray is ill conditioned, so
+    every one of the 876,096 hit rays is held to the plain tolerances (exit
+    position 1e-3 voxel, exit direction 1e-6 rad) with no excusal."""
+    hh, torch = gpu
+    parts, parts_t, bg, bg_t = scene
+    vol = hh.hh_build_index_field(parts_t, hh.make_grid(DIMS, 2.0, storage), f32(hi.K_GD))
+    cam = f32(hi.orbit_camera(DIMS, 0.0, 0.0, 1920, 1080))
+    params = f32(hi.params_euler_adaptive(DIMS, theta_max=hi.THETA_PAPER))
+    got = gpu_trace(hh, torch, vol, [cam], params, bg_t)[0]
+    vol4 = export_volume(hh, torch, vol, DIMS)
+    vol.close()
+    ref = oracle_lib.trace_grid(vol4, cam, params, bg, nthreads=16)
+    st = assert_parity_plain(got, ref, DIMS)
+    hit = (ref["flags"] & 1) != 0
+    ang = angle(got["exit_dir"][hit], ref["exit_dir"][hit])
+    print(f"1080p {storage} theta 3e-3: {st['hits']} hit rays, all within tolerance; exit "
+          f"direction error max {ang.max():.2e} rad, position max {st['pos_max']:.2e} voxel; "
+          f"{st['step_mismatch']} with another step count; RMSE {st['rmse']:.2e}")
+    assert st["hits"] == 876096
+
+
 def test_fullsize_8view_fp16(gpu, oracle_lib, scene):
     hh, torch = gpu
     parts, parts_t, bg, bg_t = scene
@@ -124,10 +148,13 @@ def test_fullsize_8view_fp16(gpu, oracle_lib, scene):
     vol16 = export_volume(hh, torch, v16, DIMS)
     vol32 = export_volume(hh, torch, v32, DIMS)
     for i, (c, g) in enumerate(zip(cams, got)):
-        pix = _sample_pixels(c, 1000, seed=100 + i, flags=g["flags"])
+        pix = _sample_pixels(c, 4000, seed=100 + i, flags=g["flags"])
         ref = oracle_lib.trace_grid(vol16, c, params, bg, pixels=pix, nthreads=8)
+        # the share of ill-conditioned rays depends on how much of the noisy
+        # plume core a view's rays cross: 0.15 % to 0.9 % of the sampled hit
+        # rays on these views (0.3 % on the whole azimuth-0 frame)
         assert_parity_conditioned(g, ref, oracle_lib, {"kind": "grid", "vol4": vol16}, DIMS, c,
-                                  params, sel=pix)
+                                  params, sel=pix, max_ill_frac=0.015)
         truth = oracle_lib.trace_grid(vol32, c, params, bg, pixels=pix, nthreads=8)
         mse = np.mean((g["rgb"][pix] - truth["rgb"]) ** 2)
         assert 10 * np.log10(1.0 / max(mse, 1e-30)) >= 50.0
@@ -193,12 +220,13 @@ def test_fullsize_512_fp16_32_views_batched(gpu, oracle_lib):
     field = {"kind": "grid", "vol4": vol4}
     hits = ill = pop_ill = 0
     for i, (c, g) in enumerate(zip(cams, got)):
-        pix = _sample_pixels(c, 128, seed=300 + i, flags=g["flags"])
+        pix = _sample_pixels(c, 4000, seed=300 + i, flags=g["flags"])
         ref = oracle_lib.trace_grid(vol4, c, params, bg, pixels=pix, nthreads=16)
-        # every ray is held to the rule; how many may be excused is counted
-        # over the whole sample below (a view holds ~64 hits)
+        # rays about twice as long as at 256^3 (~165 steps): the share of
+        # ill-conditioned rays grows with the path (measured 2.6 % of the hit
+        # rays beyond tolerance, every one ill conditioned)
         st = assert_parity_conditioned(g, ref, oracle_lib, field, dims, c, params, sel=pix,
-                                       max_ill_frac=1.0)
+                                       max_ill_frac=0.04)
         hits += st["hits"]
         ill += st["n_ill"]
         hit_pix = pix[(ref["flags"] & 1) != 0]
@@ -206,10 +234,9 @@ def test_fullsize_512_fp16_32_views_batched(gpu, oracle_lib):
             pop_ill += int(ill_conditioned(oracle_lib, field, dims, c, params, hit_pix)[0].sum())
     print(f"512^3 FP16, 32 views: {hits} sampled hit rays; the oracle alone finds {pop_ill} "
           f"ill conditioned; {ill} GPU rays beyond tolerance, all of them ill conditioned")
-    assert hits >= 1200
-    # rays are about twice as long as at 256^3 (~165 steps), and the share of
-    # ill-conditioned rays grows with them: no more rays are excused than the
-    # oracle itself finds ill conditioned in the sample
+    assert hits >= 32 * 1500
+    # no more rays are excused than the oracle itself finds ill conditioned
+    # in the sample
     assert ill <= pop_ill + 2
 
 
@@ -270,14 +297,14 @@ def test_fullsize_serve_384_fp16(gpu, oracle_lib):
     vol4 = export_volume(hh, torch, vols[f], dims)
     for v in vols:
         v.close()
-    pix = _sample_pixels(cams[0], 400, seed=500, flags=first["flags"])
+    pix = _sample_pixels(cams[0], 4000, seed=500, flags=first["flags"])
     ref = oracle_lib.trace_grid(vol4, cams[0], params, bg, pixels=pix, nthreads=16)
     field = {"kind": "grid", "vol4": vol4}
-    # rays 1.5 times as long as at 256^3: as at 512^3, no more rays are excused
-    # than the oracle alone finds ill conditioned in the sample
+    # rays 1.5 times as long as at 256^3: no more rays are excused than the
+    # oracle alone finds ill conditioned in the sample
     st = assert_parity_conditioned(first, ref, oracle_lib, field, dims, cams[0], params, sel=pix,
-                                   max_ill_frac=1.0)
-    assert st["hits"] >= 100
+                                   max_ill_frac=0.03)
+    assert st["hits"] >= 1000
     hit_pix = pix[(ref["flags"] & 1) != 0]
     pop_ill = int(ill_conditioned(oracle_lib, field, dims, cams[0], params, hit_pix)[0].sum())
     assert st["n_ill"] <= pop_ill + 2
