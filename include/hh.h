@@ -64,6 +64,8 @@ typedef enum {
 #define HH_FLAG_HIT 1u      /* the primary ray entered the volume box          */
 #define HH_FLAG_EXITED 2u   /* it left the box through the exit clip           */
 #define HH_FLAG_MAXSTEPS 4u /* it used max_steps steps without leaving the box */
+#define HH_FLAG_CLAMP 8u    /* HH_DEBUG_BOUNDS builds only: a trilinear corner  */
+                            /* index fell outside the padded volume (clamped)  */
 
 /* SPH particles, Sec. 3.1 Eq. 1 reduced to what the splat reads: n records of
  * float4 {x, y, z, m} on the device, positions in voxel units. */
@@ -205,8 +207,7 @@ hh_status hh_volume_rebuild(hh_volume vol, const hh_particles* particles, float 
  * owns the whole device-memory budget and forbids libraries from allocating,
  * or a real-time frame loop that must not pay cudaMalloc's implicit device
  * synchronisation and unbounded latency). Same computation as
- * hh_build_index_field (Sec. 3.3.1, Eqs. 12-13) with FP32 storage, but the
- * density grid lives in a
+ * hh_build_index_field with FP32 storage, but the density grid lives in a
  * fixed device array compiled into the library (8 MiB, held on every device
  * that loads the library until the process exits) and the result is written
  * to the caller's vol4_dev: nx*ny*nz*4 floats {dn, gx, gy, gz} per voxel,
@@ -483,6 +484,25 @@ const char* hh_last_error(void);
 /* Number of kernels this library has launched in this process (diagnostics,
  * no paper passage; graph replays count one each). */
 uint64_t hh_kernel_launch_count(void);
+
+/* Number of device (cudaMalloc) and pinned host (cudaMallocHost) buffers the
+ * library holds right now, across all its objects (diagnostics, no paper
+ * passage): a call that fails returns it to its value before the call. For
+ * tests of the out-of-memory paths, the environment variable
+ * HH_FAIL_ALLOC_AT=k makes the library's k-th allocation, counted from the
+ * last change of the variable's value, fail as cudaErrorMemoryAllocation
+ * (the calling entry point then returns HH_ERR_OOM); unset, nothing fails. */
+int64_t hh_live_allocations(void);
+
+/* Bounds checking of the march's volume reads (diagnostics, no paper
+ * passage). A library compiled with -DHH_DEBUG_BOUNDS (the build script's
+ * "debug_bounds" variant, libhh_debug_bounds.so) checks every trilinear
+ * corner index of every march against the padded volume, counts those
+ * outside it on the device, clamps them and sets HH_FLAG_CLAMP on the ray.
+ * This call synchronises the device and returns the count in *count
+ * (resetting it when `reset` is non-zero). In the normal build, which has no
+ * check, it sets *count = 0 and returns HH_ERR_NOT_FOUND. */
+hh_status hh_debug_bounds_violations(uint64_t* count, int reset);
 
 #ifdef __cplusplus
 }

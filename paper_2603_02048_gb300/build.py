@@ -2,8 +2,11 @@
 
 Each source in csrc/ is compiled by nvcc in parallel into _build/, then linked
 into paper_2603_02048_gb300/libhh.so against the shared CUDA runtime (the one
-PyTorch also loads, so streams are interchangeable). Usage:
-    python -m paper_2603_02048_gb300.build
+PyTorch also loads, so streams are interchangeable). The "debug_bounds"
+variant (libhh_debug_bounds.so, compiled with -DHH_DEBUG_BOUNDS) checks every
+trilinear corner index of the march against the padded volume; the tests
+build it on demand. Usage:
+    python -m paper_2603_02048_gb300.build [--variant debug_bounds]
 """
 from __future__ import annotations
 
@@ -20,6 +23,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libhh.so")
+VARIANTS = {None: ("libhh.so", "", ()), "debug_bounds": ("libhh_debug_bounds.so", "debug_bounds",
+                                                        ("-DHH_DEBUG_BOUNDS",))}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -44,8 +49,8 @@ def _stale(lib: str) -> bool:
     return any(os.path.getmtime(f) > t for f in _sources() + _headers() + [__file__])
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra, build_dir: str) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj, *extra]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -54,26 +59,32 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compiles csrc/ into libhh.so unless it is up to date; returns its path."""
-    if not force and not _stale(LIB):
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), variant=None) -> str:
+    """Compiles csrc/ into libhh.so (or the named variant's library) unless it
+    is up to date; returns its path."""
+    name, sub, defs = VARIANTS[variant]
+    lib = os.path.join(PKG, name)
+    if not force and not _stale(lib):
+        return lib
+    build_dir = os.path.join(BUILD, sub) if sub else BUILD
+    os.makedirs(build_dir, exist_ok=True)
     srcs = _sources()
+    flags = list(defs) + list(extra)
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, flags, build_dir), srcs))
+    tmp = lib + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib)
+    return lib
 
 
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True,
-          extra=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else ())
+          extra=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else (),
+          variant="debug_bounds" if "debug_bounds" in sys.argv else None)

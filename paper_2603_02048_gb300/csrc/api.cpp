@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "hh_internal.h"
@@ -39,6 +40,62 @@ hh_status ok() {
     t_last_error.clear();
     return HH_OK;
 }
+
+// Allocation wrappers: every device and pinned-host buffer the library owns
+// goes through them, so the live count below is the library's whole
+// footprint. HH_FAIL_ALLOC_AT=k makes the k-th allocation (counted from the
+// last change of the variable's value) fail with cudaErrorMemoryAllocation
+// without allocating, which drives each entry point's out-of-memory path on
+// demand.
+namespace {
+std::mutex g_alloc_mutex;
+std::string g_fail_spec;
+long g_fail_count = 0;
+std::atomic<int64_t> g_live_allocs{0};
+
+bool injected_failure() {
+    const char* spec = std::getenv("HH_FAIL_ALLOC_AT");
+    if (!spec || !*spec) return false;
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    if (g_fail_spec != spec) {
+        g_fail_spec = spec;
+        g_fail_count = 0;
+    }
+    return ++g_fail_count == std::atol(spec);
+}
+}  // namespace
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+    else *p = nullptr;
+    return e;
+}
+
+void dev_free(void* p) {
+    if (!p) return;
+    cudaFree(p);
+    g_live_allocs.fetch_sub(1);
+}
+
+cudaError_t host_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocHost(p, bytes);
+    if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+    else *p = nullptr;
+    return e;
+}
+
+void host_free(void* p) {
+    if (!p) return;
+    cudaFreeHost(p);
+    g_live_allocs.fetch_sub(1);
+}
+
+int64_t live_allocations() { return g_live_allocs.load(); }
 
 namespace {
 
@@ -93,14 +150,14 @@ hh_status new_volume(const hh_grid* g, hh_volume* out) {
     const size_t padded = static_cast<size_t>(v->bxy) * brick2_count(g->nz) * 8;
     v->bytes = padded * (g->storage == HH_STORE_FP32 ? 16 : 8);
     cudaGetDevice(&v->device);
-    cudaError_t e = cudaMalloc(&v->data, v->bytes);
+    cudaError_t e = dev_alloc(&v->data, v->bytes);
     if (e == cudaSuccess) e = cudaMemset(v->data, 0, v->bytes);  // even-padding voxels read as 0
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&v->scales_dev), 2 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&v->max_dev), 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void**>(&v->scales_dev), 2 * sizeof(float));
+    if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void**>(&v->max_dev), 2 * sizeof(unsigned));
     if (e != cudaSuccess) {
-        cudaFree(v->data);
-        cudaFree(v->scales_dev);
-        cudaFree(v->max_dev);
+        dev_free(v->data);
+        dev_free(v->scales_dev);
+        dev_free(v->max_dev);
         delete v;
         return cuda_fail(e, "volume allocation");
     }
@@ -110,12 +167,12 @@ hh_status new_volume(const hh_grid* g, hh_volume* out) {
 
 void drop_volume(hh_volume v) {
     if (!v) return;
-    cudaFree(v->rho_dev);
-    cudaFree(v->sorted_dev);
-    cudaFree(v->bins_dev);
-    cudaFree(v->data);
-    cudaFree(v->scales_dev);
-    cudaFree(v->max_dev);
+    dev_free(v->rho_dev);
+    dev_free(v->sorted_dev);
+    dev_free(v->bins_dev);
+    dev_free(v->data);
+    dev_free(v->scales_dev);
+    dev_free(v->max_dev);
     delete v;
 }
 
@@ -141,7 +198,7 @@ bool sort_particles(const hh_volume_s* v, int64_t n) {
 hh_status sort_scratch(hh_volume_s* v, int64_t n) {
     if (!v->bins_dev) {
         v->n_bins = splat_bin_count(v->nx, v->ny, v->nz);
-        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&v->bins_dev),
+        cudaError_t e = dev_alloc(reinterpret_cast<void**>(&v->bins_dev),
                                    2 * static_cast<size_t>(v->n_bins) * sizeof(unsigned));
         if (e != cudaSuccess) {
             v->bins_dev = nullptr;
@@ -149,10 +206,10 @@ hh_status sort_scratch(hh_volume_s* v, int64_t n) {
         }
     }
     if (v->sorted_cap < n) {
-        cudaFree(v->sorted_dev);
+        dev_free(v->sorted_dev);
         v->sorted_dev = nullptr;
         v->sorted_cap = 0;
-        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&v->sorted_dev),
+        cudaError_t e = dev_alloc(reinterpret_cast<void**>(&v->sorted_dev),
                                    static_cast<size_t>(n) * sizeof(float4));
         if (e != cudaSuccess) {
             v->sorted_dev = nullptr;
@@ -250,6 +307,8 @@ const char* hh_last_error(void) { return t_last_error.c_str(); }
 
 uint64_t hh_kernel_launch_count(void) { return g_launches.load(); }
 
+int64_t hh_live_allocations(void) { return live_allocations(); }
+
 hh_status hh_splat_density(const hh_particles* particles, const hh_grid* grid, float* rho_dev,
                            void* stream) {
     hh_status st = check_grid(grid, true);
@@ -285,7 +344,7 @@ hh_status hh_build_index_field(const hh_particles* particles, const hh_grid* gri
     if (!std::isfinite(K_gd)) return fail(HH_ERR_INVALID_ARG, "K_gd must be finite");
     hh_volume v = nullptr;
     if ((st = new_volume(grid, &v)) != HH_OK) return st;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&v->rho_dev), voxels(grid) * sizeof(float));
+    cudaError_t e = dev_alloc(reinterpret_cast<void**>(&v->rho_dev), voxels(grid) * sizeof(float));
     if (e != cudaSuccess) {
         drop_volume(v);
         return cuda_fail(e, "density scratch");
@@ -308,7 +367,7 @@ hh_status hh_volume_rebuild(hh_volume vol, const hh_particles* particles, float 
         return fail(HH_ERR_INVALID_ARG, "volume has no splat kernel radius (h_kernel <= 0)");
     const size_t nvox = static_cast<size_t>(vol->nx) * vol->ny * vol->nz;
     if (!vol->rho_dev) {
-        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&vol->rho_dev), nvox * sizeof(float));
+        cudaError_t e = dev_alloc(reinterpret_cast<void**>(&vol->rho_dev), nvox * sizeof(float));
         if (e != cudaSuccess) {
             vol->rho_dev = nullptr;
             return cuda_fail(e, "density scratch");

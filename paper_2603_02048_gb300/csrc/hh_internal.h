@@ -72,6 +72,15 @@ hh_status fail(hh_status st, const char* fmt, ...);
 hh_status cuda_fail(cudaError_t e, const char* what);
 hh_status ok();
 
+// Device (cudaMalloc) and pinned host (cudaMallocHost) allocations of the
+// library, counted; HH_FAIL_ALLOC_AT=k fails the k-th one (defined in
+// api.cpp). The free functions accept NULL.
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+cudaError_t host_alloc(void** p, size_t bytes);
+void host_free(void* p);
+int64_t live_allocations();
+
 // Argument checks shared by the trace entry points (defined in api.cpp).
 hh_status check_params(const hh_step_params* P);
 hh_status check_camera(const hh_camera& c, int i);

@@ -185,13 +185,36 @@ __device__ __forceinline__ float4 ld_fp16(const ushort4* __restrict__ v, unsigne
 // Trilinear sample of {dn, g} at lattice coordinate u = position + 1/2
 // (Sec. 3.3.1: n and grad n sampled with trilinear interpolation); FP16
 // volumes are interpolated as stored and scaled once afterwards.
+// With HH_DEBUG_BOUNDS the corner indices are checked against the padded
+// axes (ix in [0, nx], so that ix + 1 <= nx + 1): a corner outside is counted
+// in g_bounds_violations, flagged on the ray (HH_FLAG_CLAMP in `flags`) and
+// clamped before the load. The release build has no check and no clamp.
+#ifdef HH_DEBUG_BOUNDS
+__device__ unsigned long long g_bounds_violations;
+#endif
+
 template <int STORAGE, bool CLAMP>
-__device__ __forceinline__ Sample fetch(const VolArgs& A, float3 u, float s_n, float s_g) {
+__device__ __forceinline__ Sample fetch(const VolArgs& A, float3 u, float s_n, float s_g,
+                                        uint32_t& flags) {
     int ix, iy, iz;
     float fx, fy, fz;
     axis_cell<CLAMP>(u.x, A.nx, ix, fx);
     axis_cell<CLAMP>(u.y, A.ny, iy, fy);
     axis_cell<CLAMP>(u.z, A.nz, iz, fz);
+#ifdef HH_DEBUG_BOUNDS
+    if (ix < 0 || ix > A.nx || iy < 0 || iy > A.ny || iz < 0 || iz > A.nz) {
+        atomicAdd(&g_bounds_violations, 1ull);
+        flags |= HH_FLAG_CLAMP;
+        ix = min(max(ix, 0), A.nx);
+        iy = min(max(iy, 0), A.ny);
+        iz = min(max(iz, 0), A.nz);
+        fx = fminf(fmaxf(fx, 0.0f), 1.0f);
+        fy = fminf(fmaxf(fy, 0.0f), 1.0f);
+        fz = fminf(fmaxf(fz, 0.0f), 1.0f);
+    }
+#else
+    (void)flags;
+#endif
     // BRICK2 element of corner (ix, iy, iz), then the steps to the other
     // corners: +1 in x stays in the brick (slot +1) when ix is even, else it
     // moves to the next brick (slot -1, brick +1: +7); likewise y (+2 or
@@ -442,8 +465,9 @@ __device__ __forceinline__ float exit_fraction(const VolArgs& A, float3 hi, floa
 
 template <int STORAGE, bool CLAMP>
 __device__ __forceinline__ float3 perp_rate(const VolArgs& A, float3 u, float3 w, float s_n,
-                                            float s_g, float& n, float& gperp_norm) {
-    const Sample s = fetch<STORAGE, CLAMP>(A, u, s_n, s_g);
+                                            float s_g, float& n, float& gperp_norm,
+                                            uint32_t& flags) {
+    const Sample s = fetch<STORAGE, CLAMP>(A, u, s_n, s_g, flags);
     n = 1.0f + s.dn;
     const float3 g = make_float3(s.gx, s.gy, s.gz);
     const float3 gp = fma3(-dot(w, g), w, g);
@@ -516,21 +540,24 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     if (STEPPER == HH_STEP_RK4) {
         float n1, gpn, n2, n3, n4, unused;
         const float3 w1 = wr + d;
-        const float3 gp1 = perp_rate<STORAGE, true>(V, C, w1, R.sn, R.sg, n1, gpn);
+        const float3 gp1 = perp_rate<STORAGE, true>(V, C, w1, R.sn, R.sg, n1, gpn, R.flags);
         ds = step_length<ADAPTIVE>(V, n1, gpn);
         const float hds = 0.5f * ds;
         const float3 k1 = __fdividef(1.0f, n1) * gp1;
         const float3 d2 = fma3(hds, k1, d);
         const float3 w2 = wr + d2;
-        const float3 gp2 = perp_rate<STORAGE, true>(V, fma3(hds, w1, C), w2, R.sn, R.sg, n2, unused);
+        const float3 gp2 = perp_rate<STORAGE, true>(V, fma3(hds, w1, C), w2, R.sn, R.sg, n2, unused,
+                                                    R.flags);
         const float3 k2 = __fdividef(1.0f, n2) * gp2;
         const float3 d3 = fma3(hds, k2, d);
         const float3 w3 = wr + d3;
-        const float3 gp3 = perp_rate<STORAGE, true>(V, fma3(hds, w2, C), w3, R.sn, R.sg, n3, unused);
+        const float3 gp3 = perp_rate<STORAGE, true>(V, fma3(hds, w2, C), w3, R.sn, R.sg, n3, unused,
+                                                    R.flags);
         const float3 k3 = __fdividef(1.0f, n3) * gp3;
         const float3 d4 = fma3(ds, k3, d);
         const float3 w4 = wr + d4;
-        const float3 gp4 = perp_rate<STORAGE, true>(V, fma3(ds, w3, C), w4, R.sn, R.sg, n4, unused);
+        const float3 gp4 = perp_rate<STORAGE, true>(V, fma3(ds, w3, C), w4, R.sn, R.sg, n4, unused,
+                                                    R.flags);
         const float3 k4 = __fdividef(1.0f, n4) * gp4;
         const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
         const float3 dsum = fma3(ds * (1.0f / 6.0f), ksum, d);
@@ -540,7 +567,7 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     } else {
         float n, gpn;
         const float3 w = wr + d;
-        const float3 gp = perp_rate<STORAGE, false>(V, C, w, R.sn, R.sg, n, gpn);
+        const float3 gp = perp_rate<STORAGE, false>(V, C, w, R.sn, R.sg, n, gpn, R.flags);
         ds = step_length<ADAPTIVE>(V, n, gpn);
         const float3 d1 = fma3(__fdividef(ds, n), gp, d);
         // Eq. 16: w' = normalize(w1), C' = C + ds w'; with w' = (1 + r) w1
@@ -1080,10 +1107,10 @@ hh_status hh_batch_create(hh_volume vol, const hh_camera* cams, int n_cams,
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->views_dev), n_cams * sizeof(hh::ViewArgs));
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->counter_dev), sizeof(unsigned));
+    cudaError_t e = hh::dev_alloc(reinterpret_cast<void**>(&b->views_dev), n_cams * sizeof(hh::ViewArgs));
+    if (e == cudaSuccess) e = hh::dev_alloc(reinterpret_cast<void**>(&b->counter_dev), sizeof(unsigned));
     if (e != cudaSuccess) {
-        cudaFree(b->views_dev);
+        hh::dev_free(b->views_dev);
         delete b;
         return cuda_fail(e, "batch allocation");
     }
@@ -1214,11 +1241,31 @@ hh_status hh_batch_autotune(hh_batch b, int reps, void* stream, hh_batch_config*
     return hh::ok();
 }
 
+hh_status hh_debug_bounds_violations(uint64_t* count, int reset) {
+    if (!count) return fail(HH_ERR_INVALID_ARG, "count is NULL");
+#ifdef HH_DEBUG_BOUNDS
+    unsigned long long c = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&c, hh::g_bounds_violations, sizeof c);
+    if (e == cudaSuccess && reset) {
+        const unsigned long long zero = 0;
+        e = cudaMemcpyToSymbol(hh::g_bounds_violations, &zero, sizeof zero);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "reading the bounds counter");
+    *count = c;
+    return hh::ok();
+#else
+    (void)reset;
+    *count = 0;
+    return fail(HH_ERR_NOT_FOUND, "this library was built without HH_DEBUG_BOUNDS");
+#endif
+}
+
 hh_status hh_batch_free(hh_batch b) {
     if (!b) return hh::ok();
     drop_graph(b);
-    cudaFree(b->views_dev);
-    cudaFree(b->counter_dev);
+    hh::dev_free(b->views_dev);
+    hh::dev_free(b->counter_dev);
     delete b;
     return hh::ok();
 }

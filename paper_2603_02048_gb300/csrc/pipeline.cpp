@@ -84,8 +84,8 @@ struct hh_pipeline_s {
     ~hh_pipeline_s() {
         for (PipeSlot& s : slot) {
             if (s.batch) hh_batch_free(s.batch);
-            cudaFree(s.parts_dev);
-            cudaFree(s.rgb8_dev);
+            hh::dev_free(s.parts_dev);
+            hh::dev_free(s.rgb8_dev);
             if (s.uploaded) cudaEventDestroy(s.uploaded);
             if (s.rendered) cudaEventDestroy(s.rendered);
             if (s.downloaded) cudaEventDestroy(s.downloaded);
@@ -144,9 +144,9 @@ hh_status hh_pipeline_create(const hh_grid* grid, float K_gd, int64_t max_partic
         return st;
     }
     for (PipeSlot& s : p->slot) {
-        e = cudaMalloc(reinterpret_cast<void**>(&s.parts_dev),
+        e = hh::dev_alloc(reinterpret_cast<void**>(&s.parts_dev),
                        static_cast<size_t>(std::max<int64_t>(max_particles, 1)) * 16);
-        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s.rgb8_dev), total);
+        if (e == cudaSuccess) e = hh::dev_alloc(reinterpret_cast<void**>(&s.rgb8_dev), total);
         for (cudaEvent_t* ev : {&s.uploaded, &s.rendered, &s.downloaded})
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e != cudaSuccess) {

@@ -257,7 +257,7 @@ hh_status hh_serve_create(size_t mem_budget_bytes, int max_slots, hh_server* out
     if (!S) return hh::fail(HH_ERR_OOM, "host allocation failed");
     cudaGetDevice(&S->device);
     cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, S->device);
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&S->pool_base), mem_budget_bytes);
+    cudaError_t e = hh::dev_alloc(reinterpret_cast<void**>(&S->pool_base), mem_budget_bytes);
     if (e != cudaSuccess) {
         delete S;
         return hh::cuda_fail(e, "server memory budget");
@@ -267,9 +267,9 @@ hh_status hh_serve_create(size_t mem_budget_bytes, int max_slots, hh_server* out
     for (auto& s : S->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMallocHost(&s.table_host, kMaxViews * hh::view_record_bytes());
-        if (e == cudaSuccess) e = cudaMalloc(&s.table_dev, kMaxViews * hh::view_record_bytes());
-        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s.counter), sizeof(unsigned));
+        if (e == cudaSuccess) e = hh::host_alloc(&s.table_host, kMaxViews * hh::view_record_bytes());
+        if (e == cudaSuccess) e = hh::dev_alloc(&s.table_dev, kMaxViews * hh::view_record_bytes());
+        if (e == cudaSuccess) e = hh::dev_alloc(reinterpret_cast<void**>(&s.counter), sizeof(unsigned));
     }
     if (e != cudaSuccess) {
         hh_status st = hh::cuda_fail(e, "server slots");
@@ -474,11 +474,11 @@ hh_status hh_serve_destroy(hh_server S) {
         if (s.stream) cudaStreamSynchronize(s.stream);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.done) cudaEventDestroy(s.done);
-        if (s.table_host) cudaFreeHost(s.table_host);
-        if (s.table_dev) cudaFree(s.table_dev);
-        if (s.counter) cudaFree(s.counter);
+        if (s.table_host) hh::host_free(s.table_host);
+        if (s.table_dev) hh::dev_free(s.table_dev);
+        if (s.counter) hh::dev_free(s.counter);
     }
-    cudaFree(S->pool_base);
+    hh::dev_free(S->pool_base);
     delete S;
     return hh::ok();
 }

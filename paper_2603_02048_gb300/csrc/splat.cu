@@ -249,8 +249,13 @@ cudaError_t launch_bin_particles(const float4* xyzm, int64_t n, int nx, int ny, 
     cudaError_t e = cudaMemsetAsync(bins, 0, static_cast<size_t>(nb) * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const int threads = 256;
+    // grid-stride kernels: at most 16 resident 256-thread blocks per SM
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
     const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((n + threads - 1) / threads,
-                                                                    152 * 16));
+                                                                    int64_t(sms) * 16));
     bin_count_kernel<<<blocks, threads, 0, s>>>(xyzm, n, g, bins);
     bin_scan_kernel<<<1, 1024, 0, s>>>(bins, bins + nb, nb);
     bin_scatter_kernel<<<blocks, threads, 0, s>>>(xyzm, n, g, bins + nb, sorted);

@@ -8,6 +8,7 @@ CPU fallback: if the library is missing or fails to load, every call raises.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 
@@ -171,6 +172,8 @@ SIGNATURES = {
     "hh_serve_destroy": (ctypes.c_int, [_P]),
     "hh_last_error": (ctypes.c_char_p, []),
     "hh_kernel_launch_count": (ctypes.c_uint64, []),
+    "hh_live_allocations": (ctypes.c_int64, []),
+    "hh_debug_bounds_violations": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]),
 }
 
 _lib = None
@@ -664,3 +667,29 @@ def hh_last_error() -> str:
 
 def hh_kernel_launch_count() -> int:
     return int(load().hh_kernel_launch_count())
+
+
+def hh_live_allocations() -> int:
+    return int(load().hh_live_allocations())
+
+
+def hh_debug_bounds_violations(reset: bool = True) -> int:
+    """Corner indices outside the padded volume counted by a bounds-checking
+    build (raises HHError NOT_FOUND on the normal build)."""
+    c = ctypes.c_uint64(0)
+    _check(load().hh_debug_bounds_violations(ctypes.byref(c), int(bool(reset))))
+    return int(c.value)
+
+
+@contextlib.contextmanager
+def library(path: str):
+    """Runs the block with the binding on another build of the library (e.g.
+    the bounds-checking variant); objects made inside must be freed inside."""
+    global _lib
+    saved = _lib
+    _lib = None
+    load(path)
+    try:
+        yield _lib
+    finally:
+        _lib = saved

@@ -68,3 +68,35 @@ def test_noalloc_rejects_grids_beyond_its_array(gpu):
     with pytest.raises(hh.HHError):
         hh.hh_build_index_field_noalloc(parts_t, hh.make_grid((16, 16, 16), 2.0, "fp16"), 1.0,
                                         vol4)
+
+
+def test_noalloc_call_allocates_no_device_memory(gpu):
+    """What the entry point is for: after a first call (which looks up the
+    array's address), further calls leave the device's free memory unchanged."""
+    hh, torch = gpu
+    K = float(np.float32(hi.K_GD))
+    dims = (96, 80, 72)
+    parts_t = torch.from_numpy(hi.plume_particles(30000, 72, seed=5)).cuda()
+    vol4 = torch.empty(dims[0] * dims[1] * dims[2] * 4, device="cuda")
+    grid = hh.make_grid(dims, 2.0, "fp32")
+    hh.hh_build_index_field_noalloc(parts_t, grid, K, vol4)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        hh.hh_build_index_field_noalloc(parts_t, grid, K, vol4)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_rejects_null_particles(gpu):
+    """n > 0 with a NULL particle array is refused before any launch."""
+    import ctypes
+
+    hh, torch = gpu
+    vol4 = torch.empty(16 * 16 * 16 * 4, device="cuda")
+    parts = hh.hh_particles(None, 100)
+    grid = hh.make_grid((16, 16, 16), 2.0, "fp32")
+    st = hh.load().hh_build_index_field_noalloc(ctypes.byref(parts), ctypes.byref(grid), 1.0,
+                                                ctypes.c_void_p(vol4.data_ptr()), None)
+    assert st == 1  # HH_ERR_INVALID_ARG
+    assert "particles" in hh.hh_last_error()
