@@ -281,14 +281,22 @@ typedef struct {
                           at least this many lanes of the warp are idle (1..32;
                           32 = only when the whole warp is idle)              */
     int tile_w;        /* pixel tile of a warp: tile_w x (32 / tile_w), 4/8/16 */
+    int tile_order;    /* order in which warps take tiles: 0 = view after view,
+                          row by row; 1 = the tiles of all views interleaved
+                          by their relative row, so every view sweeps the
+                          volume top to bottom at once (views at similar
+                          elevations then share the bricks in L2: 10 % less
+                          DRAM traffic on the 512^3 32-view batch). The
+                          render server's per-request launches use 0.     */
 } hh_batch_config;
 
 /* Creates a batch of n_cams views (1..4096) over `vol` (the multi-camera
  * rendering of Sec. 4.1); outs[i] belongs to cams[i] (same layout and rules
  * as hh_trace). The library copies the view
- * table to the device (cudaMalloc + synchronous copy); the volume, the
- * background and the output buffers stay owned by the caller and must
- * outlive the batch. Default configuration: {128, 0, 32, 8}. */
+ * table (and, for tile_order 1, the tile order) to the device (cudaMalloc +
+ * synchronous copy); the volume, the background and the output buffers stay
+ * owned by the caller and must outlive the batch. Default configuration:
+ * {128, 0, 32, 8, 0}. */
 hh_status hh_batch_create(hh_volume vol, const hh_camera* cams, int n_cams,
                           const hh_step_params* params, const hh_background* bg,
                           const hh_view_out* outs, hh_batch* out);
@@ -303,7 +311,8 @@ hh_status hh_batch_get_config(hh_batch b, hh_batch_config* cfg);
 
 /* Autotuner (a GPU scheduling search; no paper passage). Times candidate
  * configurations (tile 8x4 / 4x8 / 16x2; 64, 128, 256 threads;
- * compaction at 32, 16, 8 idle lanes; full or half occupancy) with CUDA events
+ * compaction at 32, 16, 8 idle lanes; full or half occupancy; views one
+ * after the other or interleaved: 108 in all) with CUDA events
  * on `stream`, each as the median of |reps| launches, and keeps the fastest.
  * Results are cached in the process by workload (grid, storage, schedule,
  * view resolutions); reps > 0 reuses a cached result, reps < 0 re-measures.
@@ -388,15 +397,22 @@ hh_status hh_pipeline_free(hh_pipeline p);
 
 /* A render server for requests of 1..256 views against device-resident
  * per-simulation-frame volumes (the paper's use: many cameras observing one
- * shared, time-varying refractive volume, Sec. 1 and Sec. 4.2). A worker
- * thread admits a request as soon as one of the server's slots is free and
- * its output buffers fit in the server's device-memory budget; each
- * admitted request runs as one persistent batched launch (hh_batch kernel,
- * bit-identical to hh_trace) on its slot's stream, so requests arriving while
- * others run overlap with them on the GPU. Requests that do not fit yet wait;
- * later smaller ones may pass them unless they have waited over 200 ms. A
- * request whose outputs exceed the whole budget is refused (HH_ERR_OOM).
- * Requests for a frame not yet put wait for it. All host waits are bounded. */
+ * shared, time-varying refractive volume, Sec. 1 and Sec. 4.2), with
+ * ray-level continuous batching: one persistent worker kernel takes 32-pixel
+ * tiles of every admitted request from a device queue that a host thread
+ * appends to while it runs, so a new request's rays start as soon as warps
+ * free up, beside those of the requests already on the GPU (per-ray results
+ * bit-identical to hh_trace). A request is admitted while fewer than
+ * max_slots are on the GPU and its outputs fit in the server's device-memory
+ * budget; requests that do not fit yet wait (later smaller ones may pass
+ * them unless they have waited over 200 ms); a request whose outputs exceed
+ * the whole budget is refused (HH_ERR_OOM); requests for a frame not yet put
+ * wait for it. Requests with another step schedule, background or grid than
+ * the running ones wait for those to finish. Every wait is bounded: the
+ * host's, and the worker's (its warps leave after about 2 ms without work, and
+ * the host launches it again when work arrives; a request whose queue entry
+ * does not reach the device within about 5 ms of its publication fails with
+ * HH_ERR_TIMEOUT instead of being waited for). */
 typedef struct hh_server_s* hh_server;
 
 /* Outputs a request asks for (rgb is always written). */
@@ -410,15 +426,25 @@ typedef struct {
     uint64_t pending, running;  /* now                                      */
     uint64_t rays_completed;    /* primary rays of completed requests       */
     size_t pool_used, pool_capacity; /* bytes of the output budget         */
+    uint64_t worker_launches;   /* launches of the persistent worker        */
+    uint64_t worker_idle_exits; /* launches that ended by their idle limit  */
+    uint64_t entry_timeouts;    /* requests failed because the worker's
+                                   bounded wait for their queue entry ran
+                                   out (HH_ERR_TIMEOUT)                     */
 } hh_serve_stats;
 
 /* Creates a server (the multi-camera serving above, Secs. 1 and 4.2) on the
- * current device with `mem_budget_bytes` of output memory (one cudaMalloc; HH_ERR_OOM if the device cannot provide it) and
- * `max_slots` concurrent requests (1..64, one stream each). */
+ * current device with `mem_budget_bytes` of output memory (one cudaMalloc;
+ * HH_ERR_OOM if the device cannot provide it), up to `max_slots` requests on
+ * the GPU at once (1..64), its device queue (about 9 MB) and a control and a
+ * worker stream. */
 hh_status hh_serve_create(size_t mem_budget_bytes, int max_slots, hh_server* out);
 
-/* Launch shape used for every request (see hh_batch_config; a GPU scheduling
- * choice, no paper passage). HH_ERR_INVALID_ARG for a shape out of range. */
+/* Launch shape of the worker (block_threads, blocks_per_sm, tile_w of
+ * hh_batch_config; refill_min and tile_order do not apply; a GPU scheduling
+ * choice, no paper passage). Waits (up to 60 s, else HH_ERR_BUSY) until no
+ * request is waiting or running. HH_ERR_INVALID_ARG for a shape out of
+ * range. */
 hh_status hh_serve_set_config(hh_server s, const hh_batch_config* cfg);
 
 /* Registers the volume of simulation frame `frame_id` (the time-varying
@@ -461,8 +487,8 @@ hh_status hh_serve_view(hh_server s, uint64_t ticket, int view, hh_view_out* out
 hh_status hh_serve_release(hh_server s, uint64_t ticket);
 
 /* Cancels a request (bookkeeping, no paper passage): a waiting one at once, a
- * running one when its launch
- * ends (its result is discarded). Cancelled requests still need releasing. */
+ * running one when its last tile ends (its result is discarded). Cancelled
+ * requests still need releasing. */
 hh_status hh_serve_cancel(hh_server s, uint64_t ticket);
 
 /* Counters of the server's life so far (hh_serve_stats; bookkeeping, no

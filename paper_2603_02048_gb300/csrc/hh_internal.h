@@ -114,6 +114,56 @@ cudaError_t launch_batch(const hh_volume_s* vol, const hh_step_params& P, const 
                          const void* views_dev, int n_views, int total_tiles, unsigned* counter,
                          const hh_batch_config& cfg, int sm_count, cudaStream_t s);
 
+// The render server's persistent worker (ray-level continuous batching).
+// The host publishes requests ("jobs") into a device queue while the worker
+// runs; its warps take 32-pixel tiles of the oldest job that still has some,
+// and the warp that finishes a job's last tile raises the job's flag in
+// host-mapped memory. Jobs are numbered from 0 since the queue's last reset;
+// the host resets the queue only while no worker runs.
+struct ServeJob {
+    const void* vol;      // the frame's volume data (BRICK2)
+    const float* scales;  // its FP16 scales on the device
+    int view_begin;       // first record of the job in the view table
+    int n_views;
+    int n_tiles;          // tiles of all its views (view tile_begin is job-relative)
+    int seq;              // the job's number; a slot holding another number is not written yet
+};
+
+// Exit reasons of a worker launch (host_ctl[1]).
+enum { HH_WORKER_IDLE = 1, HH_WORKER_STOPPED = 2 };
+// Values of a job's host flag.
+enum { HH_JOB_DONE = 1, HH_JOB_FAILED = 2 };
+
+struct ServeWorkerArgs {
+    const ServeJob* jobs;       // job table (device)
+    const void* views;          // view records (device), view_record_bytes() apart
+    unsigned* claimed;          // per job: tiles handed out (from HH_JOB_CLAIM_FAILED up: failed)
+    unsigned* done;             // per job: tiles finished
+    const int* n_jobs;          // jobs published (device; written by host copies)
+    int* first_open;            // lowest job that may still have tiles to hand out
+    const int* stop;            // non-zero: leave when idle (device; written by a host copy)
+    int* idle_warps;            // warps of this launch that count themselves idle
+    int* leave;                 // set once every started warp is idle: the launch leaves
+    int* started_warps;         // warps of this launch that have started (all three zeroed per launch)
+    volatile unsigned* host_done;  // per job, host-mapped: HH_JOB_DONE / HH_JOB_FAILED
+    volatile int* host_ctl;     // host-mapped: [1] exit reason
+    int tile_w;
+    unsigned long long idle_ns;   // a warp leaves after this long with an empty queue
+    unsigned long long entry_ns;  // a published job's entry missing this long fails it
+};
+// A failed job's claim counter is ORed with this bit: every later claim then
+// reads as beyond the job's tiles (jobs hold fewer than 2^30 tiles, and fewer
+// than 2^31 claims follow).
+#define HH_JOB_CLAIM_FAILED 0x80000000u
+
+// Resident blocks per SM of the worker for a launch shape, and its launch
+// (VolArgs from `like`: dims, storage, schedule, background; the volume data
+// and scales come from each job).
+int serve_worker_blocks_per_sm(int storage, int stepper, int adaptive, int threads);
+cudaError_t launch_serve_worker(const hh_volume_s* like, const hh_step_params& P,
+                                const hh_background& bg, const ServeWorkerArgs& W, int blocks,
+                                int threads, cudaStream_t s);
+
 cudaError_t launch_trace(const hh_volume_s* vol, const hh_camera& cam,
                          const hh_step_params& P, const hh_background& bg,
                          const hh_view_out& out, cudaStream_t s);

@@ -30,6 +30,7 @@
 // groups, and the halo lets a sample in the box skip every index clamp.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 #include <string>
@@ -194,8 +195,8 @@ __device__ unsigned long long g_bounds_violations;
 #endif
 
 template <int STORAGE, bool CLAMP>
-__device__ __forceinline__ Sample fetch(const VolArgs& A, float3 u, float s_n, float s_g,
-                                        uint32_t& flags) {
+__device__ __forceinline__ Sample fetch(const VolArgs& A, const void* __restrict__ vol, float3 u,
+                                        float s_n, float s_g, uint32_t& flags) {
     int ix, iy, iz;
     float fx, fy, fz;
     axis_cell<CLAMP>(u.x, A.nx, ix, fx);
@@ -226,7 +227,7 @@ __device__ __forceinline__ Sample fetch(const VolArgs& A, float3 u, float s_n, f
     const unsigned b010 = b + dy, b001 = b + dz, b011 = b001 + dy;
     float4 v000, v100, v010, v110, v001, v101, v011, v111;
     if (STORAGE == HH_STORE_FP32) {
-        const float4* V = static_cast<const float4*>(A.vol);
+        const float4* V = static_cast<const float4*>(vol);
         v000 = ld_fp32(V, b);
         v100 = ld_fp32(V, b + dx);
         v010 = ld_fp32(V, b010);
@@ -236,7 +237,7 @@ __device__ __forceinline__ Sample fetch(const VolArgs& A, float3 u, float s_n, f
         v011 = ld_fp32(V, b011);
         v111 = ld_fp32(V, b011 + dx);
     } else {
-        const ushort4* V = static_cast<const ushort4*>(A.vol);
+        const ushort4* V = static_cast<const ushort4*>(vol);
         v000 = ld_fp16(V, b);
         v100 = ld_fp16(V, b + dx);
         v010 = ld_fp16(V, b010);
@@ -464,10 +465,10 @@ __device__ __forceinline__ float exit_fraction(const VolArgs& A, float3 hi, floa
 }
 
 template <int STORAGE, bool CLAMP>
-__device__ __forceinline__ float3 perp_rate(const VolArgs& A, float3 u, float3 w, float s_n,
-                                            float s_g, float& n, float& gperp_norm,
-                                            uint32_t& flags) {
-    const Sample s = fetch<STORAGE, CLAMP>(A, u, s_n, s_g, flags);
+__device__ __forceinline__ float3 perp_rate(const VolArgs& A, const void* __restrict__ vol,
+                                            float3 u, float3 w, float s_n, float s_g, float& n,
+                                            float& gperp_norm, uint32_t& flags) {
+    const Sample s = fetch<STORAGE, CLAMP>(A, vol, u, s_n, s_g, flags);
     n = 1.0f + s.dn;
     const float3 g = make_float3(s.gx, s.gy, s.gz);
     const float3 gp = fma3(-dot(w, g), w, g);
@@ -500,11 +501,11 @@ __device__ __forceinline__ void tile_pixel(int p, int tile_w_log2, int& x, int& 
 }
 
 // Ray generation and slab entry (flags = HIT when the ray enters the box).
-__device__ __forceinline__ void ray_begin(const VolArgs& V, const ViewArgs& C, int px, int py,
-                                          RayState& R) {
+__device__ __forceinline__ void ray_begin(const VolArgs& V, const float* __restrict__ scales,
+                                          const ViewArgs& C, int px, int py, RayState& R) {
     R.wr = primary_ray(C, px, py);
-    R.sn = __ldg(V.scales);
-    R.sg = __ldg(V.scales + 1);
+    R.sn = __ldg(scales);
+    R.sg = __ldg(scales + 1);
     R.k = 0;
     R.flags = 0;
     R.d = make_float3(0.0f, 0.0f, 0.0f);
@@ -531,7 +532,8 @@ __device__ __forceinline__ void ray_begin(const VolArgs& V, const ViewArgs& C, i
 // Returns true when the step leaves the box: then ep / ed hold the exit
 // point on the face and the new direction.
 template <int STORAGE, int STEPPER, bool ADAPTIVE>
-__device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& ep, float3& ed) {
+__device__ __forceinline__ bool ray_step(const VolArgs& V, const void* __restrict__ vol, RayState& R,
+                                         float3& ep, float3& ed) {
     const float B = V.bias;
     const float3 wr = R.wr, d = R.d;
     const float3 C = R.c;
@@ -540,24 +542,24 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     if (STEPPER == HH_STEP_RK4) {
         float n1, gpn, n2, n3, n4, unused;
         const float3 w1 = wr + d;
-        const float3 gp1 = perp_rate<STORAGE, true>(V, C, w1, R.sn, R.sg, n1, gpn, R.flags);
+        const float3 gp1 = perp_rate<STORAGE, true>(V, vol, C, w1, R.sn, R.sg, n1, gpn, R.flags);
         ds = step_length<ADAPTIVE>(V, n1, gpn);
         const float hds = 0.5f * ds;
         const float3 k1 = __fdividef(1.0f, n1) * gp1;
         const float3 d2 = fma3(hds, k1, d);
         const float3 w2 = wr + d2;
-        const float3 gp2 = perp_rate<STORAGE, true>(V, fma3(hds, w1, C), w2, R.sn, R.sg, n2, unused,
-                                                    R.flags);
+        const float3 gp2 = perp_rate<STORAGE, true>(V, vol, fma3(hds, w1, C), w2, R.sn, R.sg, n2,
+                                                    unused, R.flags);
         const float3 k2 = __fdividef(1.0f, n2) * gp2;
         const float3 d3 = fma3(hds, k2, d);
         const float3 w3 = wr + d3;
-        const float3 gp3 = perp_rate<STORAGE, true>(V, fma3(hds, w2, C), w3, R.sn, R.sg, n3, unused,
-                                                    R.flags);
+        const float3 gp3 = perp_rate<STORAGE, true>(V, vol, fma3(hds, w2, C), w3, R.sn, R.sg, n3,
+                                                    unused, R.flags);
         const float3 k3 = __fdividef(1.0f, n3) * gp3;
         const float3 d4 = fma3(ds, k3, d);
         const float3 w4 = wr + d4;
-        const float3 gp4 = perp_rate<STORAGE, true>(V, fma3(ds, w3, C), w4, R.sn, R.sg, n4, unused,
-                                                    R.flags);
+        const float3 gp4 = perp_rate<STORAGE, true>(V, vol, fma3(ds, w3, C), w4, R.sn, R.sg, n4,
+                                                    unused, R.flags);
         const float3 k4 = __fdividef(1.0f, n4) * gp4;
         const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
         const float3 dsum = fma3(ds * (1.0f / 6.0f), ksum, d);
@@ -567,7 +569,7 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, RayState& R, float3& 
     } else {
         float n, gpn;
         const float3 w = wr + d;
-        const float3 gp = perp_rate<STORAGE, false>(V, C, w, R.sn, R.sg, n, gpn, R.flags);
+        const float3 gp = perp_rate<STORAGE, false>(V, vol, C, w, R.sn, R.sg, n, gpn, R.flags);
         ds = step_length<ADAPTIVE>(V, n, gpn);
         const float3 d1 = fma3(__fdividef(ds, n), gp, d);
         // Eq. 16: w' = normalize(w1), C' = C + ds w'; with w' = (1 + r) w1
@@ -660,11 +662,33 @@ __global__ void __launch_bounds__(128, (STEPPER == HH_STEP_RK4) ? 6 : HH_MARCH_M
     if (px >= C.W || py >= C.H) return;
     RayState R;
     float3 ep = C.eye, ed = C.eye;
-    ray_begin(V, C, px, py, R);
+    ray_begin(V, V.scales, C, px, py, R);
     if (R.flags & HH_FLAG_HIT)
-        while (R.k < V.max_steps && !ray_step<STORAGE, STEPPER, ADAPTIVE>(V, R, ep, ed)) {
+        while (R.k < V.max_steps && !ray_step<STORAGE, STEPPER, ADAPTIVE>(V, V.vol, R, ep, ed)) {
         }
     ray_end(V, C, px, py, R, ep, ed);
+}
+
+// View and view-local index of batch tile t: from the order table when
+// there is one (tiles of all views in the order the table gives), else the
+// last view whose first tile is <= t (views one after the other).
+__device__ __forceinline__ void tile_of(int t, int n_views, const int* s_begin,
+                                        const uint2* __restrict__ order, int& view,
+                                        int& local) {
+    if (order) {
+        const uint2 o = __ldg(order + t);
+        view = static_cast<int>(o.x);
+        local = static_cast<int>(o.y);
+        return;
+    }
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_begin[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    view = lo;
+    local = t - s_begin[lo];
 }
 
 // Persistent batched march over many views of uneven size. Each warp pulls
@@ -681,7 +705,7 @@ template <int STORAGE, int STEPPER, bool ADAPTIVE, bool REFILL>
 __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_MIN_BLOCKS)
     march_batch_kernel(const VolArgs V, const ViewArgs* __restrict__ views, int n_views,
                        int total_tiles, int tile_w, unsigned* __restrict__ counter,
-                       int refill_min) {
+                       int refill_min, const uint2* __restrict__ order) {
     extern __shared__ int s_begin[];  // first tile of each view, then total_tiles
     for (int i = threadIdx.x; i <= n_views; i += blockDim.x)
         s_begin[i] = i < n_views ? views[i].tile_begin : total_tiles;
@@ -698,28 +722,23 @@ __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_M
             if (lane == 0) t = static_cast<int>(atomicAdd(counter, 1u));
             t = __shfl_sync(FULL, t, 0);
             if (t >= total_tiles) return;
-            int lo = 0, hi = n_views - 1;  // last view whose first tile <= t
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_begin[mid] <= t) lo = mid;
-                else hi = mid - 1;
-            }
+            int lo, local;
+            tile_of(t, n_views, s_begin, order, lo, local);
             const ViewArgs& C = views[lo];
-            const int local = t - s_begin[lo];
             const int ty = local / C.tiles_x, tx = local - ty * C.tiles_x;
             const int px = (tx << tile_w_log2) + lx, py = ty * (32 >> tile_w_log2) + ly;
             if (px < C.W && py < C.H) {
                 RayState R;
                 float3 ep = make_float3(0.0f, 0.0f, 0.0f), ed = ep;
-                ray_begin(V, C, px, py, R);
+                ray_begin(V, V.scales, C, px, py, R);
                 if (R.flags & HH_FLAG_HIT)
-                    while (R.k < V.max_steps && !ray_step<STORAGE, STEPPER, ADAPTIVE>(V, R, ep, ed)) {
+                    while (R.k < V.max_steps && !ray_step<STORAGE, STEPPER, ADAPTIVE>(V, V.vol, R, ep, ed)) {
                     }
                 ray_end(V, C, px, py, R, ep, ed);
             }
         }
     }
-    int tile = 0, tile_view = 0, pos = 32;  // the warp's pixel stream (warp-uniform)
+    int tile_local = 0, tile_view = 0, pos = 32;  // the warp's pixel stream (warp-uniform)
     bool done = false, have = false;
     int vi = 0, px = 0, py = 0;
     RayState R;
@@ -737,14 +756,7 @@ __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_M
                         done = true;
                         break;
                     }
-                    int lo = 0, hi = n_views - 1;  // last view whose first tile <= t
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (s_begin[mid] <= t) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    tile = t;
-                    tile_view = lo;
+                    tile_of(t, n_views, s_begin, order, tile_view, tile_local);
                     pos = 0;
                 }
                 const int avail = 32 - pos;
@@ -752,7 +764,7 @@ __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_M
                 const bool mine = ((todo >> lane) & 1u) && rank < avail;
                 if (mine) {
                     const ViewArgs& C = views[tile_view];
-                    const int local = tile - s_begin[tile_view];
+                    const int local = tile_local;
                     const int p = pos + rank;
                     const int ty = local / C.tiles_x, tx = local - ty * C.tiles_x;
                     int lx, ly;
@@ -761,7 +773,7 @@ __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_M
                     py = ty * (32 >> tile_w_log2) + ly;
                     vi = tile_view;
                     if (px < C.W && py < C.H) {
-                        ray_begin(V, C, px, py, R);
+                        ray_begin(V, V.scales, C, px, py, R);
                         if ((R.flags & HH_FLAG_HIT) && V.max_steps > 0) have = true;
                         else ray_end(V, C, px, py, R, ep, ed);
                     }
@@ -775,11 +787,218 @@ __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_M
             continue;
         }
         if (have) {
-            if (ray_step<STORAGE, STEPPER, ADAPTIVE>(V, R, ep, ed) || R.k >= V.max_steps) {
+            if (ray_step<STORAGE, STEPPER, ADAPTIVE>(V, V.vol, R, ep, ed) || R.k >= V.max_steps) {
                 ray_end(V, views[vi], px, py, R, ep, ed);
                 have = false;
             }
         }
+    }
+}
+
+// The render server's persistent worker (ray-level continuous batching):
+// jobs (requests) are published by the host into a device queue while the
+// kernel runs. A warp keeps a cursor j on the job table: it waits for job j
+// to be published (n_jobs > j) and written (its entry's seq == j), takes
+// tiles of it from the job's counter until they run out, then moves on. The
+// warp that finishes a job's last tile raises the job's flag in host-mapped
+// memory. Every wait is bounded in time (the global nanosecond timer): a warp
+// whose queue has stayed empty for idle_ns counts itself idle, and once every
+// warp of the launch is idle they all leave together (a warp that finds work
+// again uncounts itself; the host launches the worker again when new work
+// arrives, so the whole grid, not a remnant of it, serves the next burst); a
+// warp told to stop leaves when idle; and a job whose entry does not appear
+// within entry_ns of its publication being seen is failed (flag
+// HH_JOB_FAILED) instead of waited for. Idle polls back off
+// from 1 to 32 us, so thousands of idle warps do not crowd the queue's cache
+// line. The per-ray arithmetic is march_kernel's (ray_begin / ray_step /
+// ray_end) on the volume of the tile's job.
+__device__ __forceinline__ int ld_acquire_int(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "l"(p), "r"(v)
+                 : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Resident 256-thread blocks per SM of the serving worker: 4 (64 registers)
+// for the Eq. 16 march, whose per-tile and per-job state lives outside the
+// step loop.
+#ifndef HH_WORKER_MIN_BLOCKS
+#define HH_WORKER_MIN_BLOCKS 4
+#endif
+
+template <int STORAGE, int STEPPER, bool ADAPTIVE>
+__global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_WORKER_MIN_BLOCKS)
+    serve_worker_kernel(const VolArgs V, const ServeWorkerArgs W) {
+    extern __shared__ __align__(16) unsigned char s_raw[];  // one view record per warp
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ViewArgs& C = reinterpret_cast<ViewArgs*>(s_raw)[warp];
+    const int tile_w_log2 = W.tile_w == 16 ? 4 : (W.tile_w == 8 ? 3 : 2);
+    const int tile_h = 32 >> tile_w_log2;
+    int lx, ly;
+    tile_pixel(lane, tile_w_log2, lx, ly);
+    const char* views = static_cast<const char*>(W.views);
+    constexpr int kWords = sizeof(ViewArgs) / sizeof(unsigned);
+    int j = ld_acquire_int(W.first_open);
+    int have_job = -1;
+    int view_first = 0, view_end = 0;  // job-relative tiles of the view in C
+    const void* jvol = nullptr;
+    const float* jscales = nullptr;
+    int jview_begin = 0, jn_views = 0, jn_tiles = 0;
+    unsigned t = 0;  // this warp's claimed tile of job j (valid while have_job == j)
+    bool claimed_next = false;
+    unsigned long long idle_since = 0;
+    unsigned backoff = 1000;
+    bool counted_idle = false;
+    if (lane == 0) atomicAdd(W.started_warps, 1);
+    for (;;) {
+        if (j != have_job) {
+            // wait for job j: published, then written (both bounded in time)
+            int ok = 0;
+            if (lane == 0) {
+                if (j < ld_acquire_int(W.n_jobs)) {
+                    ok = 1;
+                    if (*reinterpret_cast<const volatile unsigned*>(W.claimed + j) >=
+                        HH_JOB_CLAIM_FAILED) {
+                        ok = 2;  // failed by another warp: skip it
+                    } else if (ld_acquire_int(&W.jobs[j].seq) != j) {
+                        const unsigned long long t0 = global_ns();
+                        while (ld_acquire_int(&W.jobs[j].seq) != j) {
+                            if (global_ns() - t0 > W.entry_ns) {
+                                ok = 2;
+                                if (atomicOr(W.claimed + j, HH_JOB_CLAIM_FAILED) <
+                                    HH_JOB_CLAIM_FAILED) {
+                                    __threadfence_system();
+                                    W.host_done[j] = HH_JOB_FAILED;
+                                }
+                                break;
+                            }
+                            __nanosleep(1000);
+                        }
+                    }
+                } else if (ld_acquire_int(W.stop) != 0) {
+                    ok = -1;  // stop requested
+                }
+            }
+            ok = __shfl_sync(FULL, ok, 0);
+            if (ok == -1) {
+                if (lane == 0) W.host_ctl[1] = HH_WORKER_STOPPED;
+                break;
+            }
+            if (ok == 0) {  // nothing published beyond j: idle (bounded)
+                int leave = 0;
+                if (lane == 0) {
+                    const unsigned long long now = global_ns();
+                    if (idle_since == 0) idle_since = now;
+                    if (!counted_idle && now - idle_since > W.idle_ns) {
+                        counted_idle = true;
+                        // all warps that have started are idle: the launch leaves
+                        // (a block that starts later sees the flag and leaves too)
+                        if (atomicAdd(W.idle_warps, 1) + 1 == ld_acquire_int(W.started_warps))
+                            atomicExch(W.leave, 1);
+                    }
+                    leave = ld_acquire_int(W.leave);
+                }
+                if (__shfl_sync(FULL, leave, 0)) break;
+                __nanosleep(backoff);
+                backoff = min(backoff * 2u, 32000u);
+                j = max(j, ld_acquire_int(W.first_open));
+                continue;
+            }
+            if (ok == 2) {
+                ++j;
+                continue;
+            }
+            idle_since = 0;
+            backoff = 1000;
+            if (counted_idle) {
+                if (lane == 0) atomicSub(W.idle_warps, 1);
+                counted_idle = false;
+            }
+            const ServeJob* e = W.jobs + j;
+            jvol = reinterpret_cast<const void*>(
+                __ldcg(reinterpret_cast<const unsigned long long*>(&e->vol)));
+            jscales = reinterpret_cast<const float*>(
+                __ldcg(reinterpret_cast<const unsigned long long*>(&e->scales)));
+            jview_begin = __ldcg(&e->view_begin);
+            jn_views = __ldcg(&e->n_views);
+            jn_tiles = __ldcg(&e->n_tiles);
+            have_job = j;
+            view_first = view_end = 0;
+            claimed_next = false;
+        }
+        if (!claimed_next) {
+            if (lane == 0) t = atomicAdd(W.claimed + j, 1u);
+            t = __shfl_sync(FULL, t, 0);
+        }
+        claimed_next = false;
+        if (t >= static_cast<unsigned>(jn_tiles)) {  // exhausted (or failed): next job
+            ++j;
+            if (lane == 0) atomicMax(W.first_open, j);
+            continue;
+        }
+        const int ti = static_cast<int>(t);
+        if (ti < view_first || ti >= view_end) {
+            // the tile's view: the last view of the job whose first tile is <= t
+            int lo = 0, hi = jn_views - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                const ViewArgs* vm = reinterpret_cast<const ViewArgs*>(
+                    views + static_cast<size_t>(jview_begin + mid) * sizeof(ViewArgs));
+                if (__ldcg(&vm->tile_begin) <= ti) lo = mid;
+                else hi = mid - 1;
+            }
+            __syncwarp();
+            const unsigned* src = reinterpret_cast<const unsigned*>(
+                views + static_cast<size_t>(jview_begin + lo) * sizeof(ViewArgs));
+            for (int w = lane; w < kWords; w += 32) reinterpret_cast<unsigned*>(&C)[w] = __ldcg(src + w);
+            __syncwarp();
+            view_first = C.tile_begin;
+            view_end = view_first + C.tiles_x * ((C.H + tile_h - 1) / tile_h);
+        }
+        const int local = ti - view_first;
+        const int ty = local / C.tiles_x, tx = local - ty * C.tiles_x;
+        const int px = (tx << tile_w_log2) + lx, py = ty * tile_h + ly;
+        if (px < C.W && py < C.H) {
+            RayState R;
+            float3 ep = make_float3(0.0f, 0.0f, 0.0f), ed = ep;
+            ray_begin(V, jscales, C, px, py, R);
+            if (R.flags & HH_FLAG_HIT)
+                while (R.k < V.max_steps && !ray_step<STORAGE, STEPPER, ADAPTIVE>(V, jvol, R, ep, ed)) {
+                }
+            ray_end(V, C, px, py, R, ep, ed);
+        }
+        // count the tile (release: its outputs are ordered before the count,
+        // so the warp that sees the count reach n_tiles sees every tile) and
+        // claim the next one in the same breath, unless the launch is leaving
+        // (then the next launch takes the job's remaining tiles)
+        __syncwarp();
+        unsigned next = 0;
+        int leave = 0;
+        if (lane == 0) {
+            const unsigned before = atom_add_acq_rel(W.done + j, 1u);
+            leave = ld_acquire_int(W.leave);
+            if (!leave) next = atomicAdd(W.claimed + j, 1u);
+            if (before + 1u == static_cast<unsigned>(jn_tiles)) {
+                __threadfence_system();
+                W.host_done[j] = HH_JOB_DONE;
+            }
+        }
+        if (__shfl_sync(FULL, leave, 0)) break;
+        t = __shfl_sync(FULL, next, 0);
+        claimed_next = true;
     }
 }
 
@@ -815,15 +1034,32 @@ struct SingleLaunch {
 template <int ST, int SP, bool AD>
 struct BatchLaunch {
     static void run(const VolArgs& V, const ViewArgs* views, int n_views, int total_tiles,
-                    int tile_w, unsigned* counter, int refill_min, int blocks, int threads,
-                    cudaStream_t s) {
+                    int tile_w, unsigned* counter, int refill_min, const uint2* order, int blocks,
+                    int threads, cudaStream_t s) {
         const size_t smem = (n_views + 1) * sizeof(int);
         if (refill_min >= 32)
             march_batch_kernel<ST, SP, AD, false><<<blocks, threads, smem, s>>>(
-                V, views, n_views, total_tiles, tile_w, counter, refill_min);
+                V, views, n_views, total_tiles, tile_w, counter, refill_min, order);
         else
             march_batch_kernel<ST, SP, AD, true><<<blocks, threads, smem, s>>>(
-                V, views, n_views, total_tiles, tile_w, counter, refill_min);
+                V, views, n_views, total_tiles, tile_w, counter, refill_min, order);
+    }
+};
+
+template <int ST, int SP, bool AD>
+struct WorkerLaunch {
+    static void run(const VolArgs& V, const ServeWorkerArgs& W, int blocks, int threads,
+                    cudaStream_t s) {
+        const size_t smem = (threads / 32) * sizeof(ViewArgs);
+        serve_worker_kernel<ST, SP, AD><<<blocks, threads, smem, s>>>(V, W);
+    }
+};
+
+template <int ST, int SP, bool AD>
+struct WorkerOccupancy {
+    static void run(int threads, int* blocks_per_sm) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, serve_worker_kernel<ST, SP, AD>,
+                                                      threads, (threads / 32) * sizeof(ViewArgs));
     }
 };
 
@@ -962,8 +1198,24 @@ cudaError_t launch_batch(const hh_volume_s* vol, const hh_step_params& P, const 
     const VolArgs V = make_vol_args(vol, P, bg);
     dispatch<BatchLaunch>(vol->storage, P.stepper, P.adaptive, V,
                           static_cast<const ViewArgs*>(views_dev), n_views, total_tiles,
-                          cfg.tile_w, counter, cfg.refill_min, sm_count * bps, cfg.block_threads,
-                          s);
+                          cfg.tile_w, counter, cfg.refill_min, static_cast<const uint2*>(nullptr),
+                          sm_count * bps, cfg.block_threads, s);
+    count_launch();
+    return cudaGetLastError();
+}
+
+int serve_worker_blocks_per_sm(int storage, int stepper, int adaptive, int threads) {
+    int bps = 0;
+    dispatch<WorkerOccupancy>(storage, stepper, adaptive, threads, &bps);
+    return max(bps, 1);
+}
+
+cudaError_t launch_serve_worker(const hh_volume_s* like, const hh_step_params& P,
+                                const hh_background& bg, const ServeWorkerArgs& W, int blocks,
+                                int threads, cudaStream_t s) {
+    if (like->layout != HH_LAYOUT_BRICK2) return cudaErrorInvalidValue;
+    const VolArgs V = make_vol_args(like, P, bg);
+    dispatch<WorkerLaunch>(like->storage, P.stepper, P.adaptive, V, W, blocks, threads, s);
     count_launch();
     return cudaGetLastError();
 }
@@ -983,6 +1235,7 @@ struct hh_batch_s {
     int total_tiles = 0;
     hh::ViewArgs* views_dev = nullptr;
     unsigned* counter_dev = nullptr;
+    uint2* order_dev = nullptr;  // tile order table (NULL: views one after the other)
     int sm_count = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1002,6 +1255,29 @@ void drop_graph(hh_batch b) {
     b->graph_stream = nullptr;
 }
 
+// The interleaved tile order (tile_order 1): the tiles of all views sorted by
+// their relative row in their view (then by view, then by column), so that
+// every view sweeps the volume top to bottom at the same time.
+std::vector<uint2> interleaved_order(const std::vector<hh::ViewArgs>& v, int tile_w) {
+    struct Key {
+        double k;
+        uint32_t view, local;
+    };
+    std::vector<Key> keys;
+    const int tile_h = 32 / tile_w;
+    for (size_t i = 0; i < v.size(); ++i) {
+        const int tiles_y = (v[i].H + tile_h - 1) / tile_h;
+        for (int ty = 0; ty < tiles_y; ++ty)
+            for (int tx = 0; tx < v[i].tiles_x; ++tx)
+                keys.push_back({(ty + 0.5) / tiles_y, static_cast<uint32_t>(i),
+                                static_cast<uint32_t>(ty * v[i].tiles_x + tx)});
+    }
+    std::stable_sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) { return x.k < y.k; });
+    std::vector<uint2> ord(keys.size());
+    for (size_t j = 0; j < keys.size(); ++j) ord[j] = make_uint2(keys[j].view, keys[j].local);
+    return ord;
+}
+
 // Uploads the view table for the current tile width (synchronous).
 hh_status upload_views(hh_batch b) {
     std::vector<hh::ViewArgs> v(b->cams.size());
@@ -1018,6 +1294,16 @@ hh_status upload_views(hh_batch b) {
     cudaError_t e = cudaMemcpy(b->views_dev, v.data(), v.size() * sizeof(hh::ViewArgs),
                                cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "uploading the view table");
+    hh::dev_free(b->order_dev);
+    b->order_dev = nullptr;
+    if (b->cfg.tile_order == 1) {
+        std::vector<uint2> ord = interleaved_order(v, tile_w);
+        e = hh::dev_alloc(reinterpret_cast<void**>(&b->order_dev), ord.size() * sizeof(uint2));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->order_dev, ord.data(), ord.size() * sizeof(uint2),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "uploading the tile order");
+    }
     return HH_OK;
 }
 
@@ -1031,6 +1317,8 @@ hh_status check_config(const hh_batch_config* c) {
         return fail(HH_ERR_INVALID_ARG, "refill_min must be in [1, 32]");
     if (c->tile_w != 4 && c->tile_w != 8 && c->tile_w != 16)
         return fail(HH_ERR_INVALID_ARG, "tile_w must be 4, 8 or 16");
+    if (c->tile_order != 0 && c->tile_order != 1)
+        return fail(HH_ERR_INVALID_ARG, "tile_order must be 0 or 1");
     return HH_OK;
 }
 
@@ -1058,8 +1346,8 @@ cudaError_t enqueue(hh_batch b, int blocks, cudaStream_t s) {
     const hh::VolArgs V = hh::make_vol_args(b->vol, b->params, b->bg);
     hh::dispatch<hh::BatchLaunch>(b->vol->storage, b->params.stepper, b->params.adaptive, V,
                                   b->views_dev, static_cast<int>(b->cams.size()), b->total_tiles,
-                                  b->cfg.tile_w, b->counter_dev, b->cfg.refill_min, blocks,
-                                  threads, s);
+                                  b->cfg.tile_w, b->counter_dev, b->cfg.refill_min,
+                                  static_cast<const uint2*>(b->order_dev), blocks, threads, s);
     hh::count_launch();
     return cudaGetLastError();
 }
@@ -1103,7 +1391,7 @@ hh_status hh_batch_create(hh_volume vol, const hh_camera* cams, int n_cams,
     b->bg = *bg;
     b->cams.assign(cams, cams + n_cams);
     b->outs.assign(outs, outs + n_cams);
-    b->cfg = hh_batch_config{128, 0, 32, 8};
+    b->cfg = hh_batch_config{128, 0, 32, 8, 0};
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -1126,7 +1414,7 @@ hh_status hh_batch_set_config(hh_batch b, const hh_batch_config* cfg) {
     if (!b) return fail(HH_ERR_INVALID_ARG, "batch is NULL");
     hh_status st = check_config(cfg);
     if (st != HH_OK) return st;
-    const bool retile = cfg->tile_w != b->cfg.tile_w;
+    const bool retile = cfg->tile_w != b->cfg.tile_w || cfg->tile_order != b->cfg.tile_order;
     b->cfg = *cfg;
     drop_graph(b);
     if (retile && (st = upload_views(b)) != HH_OK) return st;
@@ -1192,10 +1480,11 @@ hh_status hh_batch_autotune(hh_batch b, int reps, void* stream, hh_batch_config*
     if (reps == 0) return fail(HH_ERR_INVALID_ARG, "reps must be non-zero");
     const int n = reps < 0 ? -reps : reps;
     std::vector<hh_batch_config> cand;
-    for (int tw : {8, 4, 16})
-        for (int th : {128, 256, 64})
-            for (int rm : {32, 16, 8})
-                for (int bps : {0, -2}) cand.push_back(hh_batch_config{th, bps, rm, tw});
+    for (int to : {0, 1})
+        for (int tw : {8, 4, 16})
+            for (int th : {128, 256, 64})
+                for (int rm : {32, 16, 8})
+                    for (int bps : {0, -2}) cand.push_back(hh_batch_config{th, bps, rm, tw, to});
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -1266,6 +1555,7 @@ hh_status hh_batch_free(hh_batch b) {
     drop_graph(b);
     hh::dev_free(b->views_dev);
     hh::dev_free(b->counter_dev);
+    hh::dev_free(b->order_dev);
     delete b;
     return hh::ok();
 }

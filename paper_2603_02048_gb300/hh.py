@@ -89,7 +89,8 @@ class hh_view_out(ctypes.Structure):
 
 class hh_batch_config(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("refill_min", ctypes.c_int), ("tile_w", ctypes.c_int)]
+                ("refill_min", ctypes.c_int), ("tile_w", ctypes.c_int),
+                ("tile_order", ctypes.c_int)]
 
 
 class hh_serve_stats(ctypes.Structure):
@@ -98,7 +99,8 @@ class hh_serve_stats(ctypes.Structure):
                 ("failed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("pending", ctypes.c_uint64), ("running", ctypes.c_uint64),
                 ("rays_completed", ctypes.c_uint64), ("pool_used", ctypes.c_size_t),
-                ("pool_capacity", ctypes.c_size_t)]
+                ("pool_capacity", ctypes.c_size_t), ("worker_launches", ctypes.c_uint64),
+                ("worker_idle_exits", ctypes.c_uint64), ("entry_timeouts", ctypes.c_uint64)]
 
 
 HH_OUT_RGB = 1
@@ -425,8 +427,10 @@ def hh_batch_create(vol: Volume, cams, params, bg, outs) -> Batch:
     return Batch(out, (vol, bg, outs))
 
 
-def hh_batch_set_config(b: Batch, block_threads=128, blocks_per_sm=0, refill_min=32, tile_w=8):
-    c = hh_batch_config(int(block_threads), int(blocks_per_sm), int(refill_min), int(tile_w))
+def hh_batch_set_config(b: Batch, block_threads=128, blocks_per_sm=0, refill_min=32, tile_w=8,
+                        tile_order=0):
+    c = hh_batch_config(int(block_threads), int(blocks_per_sm), int(refill_min), int(tile_w),
+                        int(tile_order))
     _check(load().hh_batch_set_config(b.handle, ctypes.byref(c)))
 
 
@@ -499,7 +503,7 @@ def hh_pipeline_create(grid: hh_grid, K_gd: float, max_particles: int, cams, par
     B = _background(bg)
     C = None if cfg is None else ctypes.byref(hh_batch_config(
         int(cfg["block_threads"]), int(cfg["blocks_per_sm"]), int(cfg["refill_min"]),
-        int(cfg["tile_w"])))
+        int(cfg["tile_w"]), int(cfg.get("tile_order", 0))))
     out = ctypes.c_void_p()
     _check(load().hh_pipeline_create(ctypes.byref(grid), float(K_gd), int(max_particles), c_cams,
                                      n, ctypes.byref(P), ctypes.byref(B), C, ctypes.byref(out)))
@@ -574,8 +578,10 @@ def hh_serve_create(mem_budget_bytes: int, max_slots: int) -> Server:
     return Server(out)
 
 
-def hh_serve_set_config(s: Server, block_threads=128, blocks_per_sm=0, refill_min=32, tile_w=8):
-    c = hh_batch_config(int(block_threads), int(blocks_per_sm), int(refill_min), int(tile_w))
+def hh_serve_set_config(s: Server, block_threads=128, blocks_per_sm=0, refill_min=32, tile_w=8,
+                        tile_order=0):
+    c = hh_batch_config(int(block_threads), int(blocks_per_sm), int(refill_min), int(tile_w),
+                        int(tile_order))
     _check(load().hh_serve_set_config(s.handle, ctypes.byref(c)))
 
 

@@ -50,10 +50,12 @@ def test_struct_layouts_match_header(lib):
                "hh_background": ["rgb8_dev", "width", "height", "n_planes", "planes"],
                "hh_plane": ["origin", "u", "v", "rgb8_dev", "width", "height"],
                "hh_view_out": ["rgb", "exit_pos", "exit_dir", "steps", "flags", "rgb8"],
-               "hh_batch_config": ["block_threads", "blocks_per_sm", "refill_min", "tile_w"],
+               "hh_batch_config": ["block_threads", "blocks_per_sm", "refill_min", "tile_w",
+                                   "tile_order"],
                "hh_serve_stats": ["submitted", "admitted", "completed", "cancelled", "failed",
                                   "rejected", "pending", "running", "rays_completed",
-                                  "pool_used", "pool_capacity"]}
+                                  "pool_used", "pool_capacity", "worker_launches",
+                                  "worker_idle_exits", "entry_timeouts"]}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"',
              "int main(void) {"]
     for s, fields in structs.items():

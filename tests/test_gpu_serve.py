@@ -193,3 +193,62 @@ def test_invalid_calls_and_budget_failure(gpu, frames):
         hh.hh_serve_set_config(srv, 128, 0, 0, 8)
     assert hh.hh_serve_poll(srv, 12345)[0] == 7
     srv.close()
+
+
+def test_worker_leaves_when_idle_and_comes_back(gpu, frames):
+    """The persistent worker's wait for work is bounded: with the queue empty
+    its warps leave after about 2 ms (an idle exit), and the next request
+    launches it again; results stay hh_trace's."""
+    hh, torch = gpu
+    dims, vols, bg, params = frames
+    srv = hh.hh_serve_create(64 << 20, 4)
+    hh.hh_serve_put_volume(srv, 0, vols[0])
+    cams = _request_views(dims, 21, 2)
+    ref = _trace_ref(hh, torch, vols[0], cams, params, bg)
+    for round_ in range(2):
+        t = hh.hh_serve_submit(srv, 0, cams, params, bg, OUTS_ALL)
+        hh.hh_serve_wait(srv, t, 20000)
+        _equal(_fetch(hh, srv, t, cams), ref)
+        hh.hh_serve_release(srv, t)
+        deadline = time.time() + 5.0
+        while hh.hh_serve_get_stats(srv)["worker_idle_exits"] < round_ + 1:
+            assert time.time() < deadline, "the worker did not leave its empty queue"
+            time.sleep(0.005)
+    st = hh.hh_serve_get_stats(srv)
+    assert st["worker_launches"] == 2 and st["worker_idle_exits"] == 2
+    assert st["completed"] == 2 and st["entry_timeouts"] == 0
+    srv.close()
+
+
+def test_missing_queue_entry_times_out_on_the_device(gpu, frames, monkeypatch):
+    """A request whose queue entry never reaches the device (the host drops
+    its copy: HH_SERVE_DROP_ENTRY) is failed by the worker's bounded wait with
+    HH_ERR_TIMEOUT; the requests before and after it are served as usual."""
+    hh, torch = gpu
+    dims, vols, bg, params = frames
+    srv = hh.hh_serve_create(64 << 20, 4)
+    hh.hh_serve_put_volume(srv, 0, vols[0])
+    cams = _request_views(dims, 22, 2)
+    ref = _trace_ref(hh, torch, vols[0], cams, params, bg)
+    monkeypatch.setenv("HH_SERVE_DROP_ENTRY", "2")  # the second job this server publishes
+    t1 = hh.hh_serve_submit(srv, 0, cams, params, bg, OUTS_ALL)
+    hh.hh_serve_wait(srv, t1, 20000)
+    t2 = hh.hh_serve_submit(srv, 0, cams, params, bg, OUTS_ALL)
+    t0 = time.time()
+    with pytest.raises(hh.HHError) as e:
+        hh.hh_serve_wait(srv, t2, 20000)
+    assert e.value.status == 4 and time.time() - t0 < 5.0  # HH_ERR_TIMEOUT from the device
+    monkeypatch.delenv("HH_SERVE_DROP_ENTRY")
+    t3 = hh.hh_serve_submit(srv, 0, cams, params, bg, OUTS_ALL)
+    hh.hh_serve_wait(srv, t3, 20000)
+    for t in (t1, t3):
+        _equal(_fetch(hh, srv, t, cams), ref)
+        hh.hh_serve_release(srv, t)
+    hh.hh_serve_release(srv, t2)
+    st = hh.hh_serve_get_stats(srv)
+    assert st["entry_timeouts"] == 1 and st["failed"] == 1 and st["completed"] == 2
+    deadline = time.time() + 5.0
+    while hh.hh_serve_get_stats(srv)["pool_used"] != 0:  # the failed one's memory comes back
+        assert time.time() < deadline
+        time.sleep(0.005)
+    srv.close()
