@@ -342,8 +342,10 @@ hh_status hh_batch_free(hh_batch b);
  * frame's particles splatted into the index volume, Sec. 3.3.1, then every
  * camera's view marched through it, Secs. 3.3.2-3.3.3), with the particles
  * coming from host memory and the display images (RGB8, as in hh_view_out)
- * going back to host memory. Frames are double buffered on three streams of
- * the library's own: while frame t is built and marched, frame t+1's
+ * going back to host memory. Frames are double buffered, each of the two
+ * slots with its own volume, buffers and compute stream, plus an upload and
+ * a download stream of the library's own: frame t+1's build runs beside
+ * frame t's march, and while frame t is built and marched, frame t+1's
  * particles are uploaded and frame t-1's images downloaded, so the copies
  * overlap the kernels. One thread drives a pipeline. */
 typedef struct hh_pipeline_s* hh_pipeline;
@@ -354,8 +356,9 @@ typedef struct hh_pipeline_s* hh_pipeline;
  * max_particles particles per frame. cfg NULL: one hh_trace launch per view;
  * otherwise the views run as one batched launch (hh_batch, bit-identical to
  * hh_trace) with that configuration, replayed from a CUDA graph. Allocates
- * on the current device the volume, two particle buffers and two sets of
- * image buffers; cams and params are copied; the background's device
+ * on the current device two volumes (one per slot, with their density
+ * scratch), two particle buffers and two sets of image buffers; cams and
+ * params are copied; the background's device
  * buffers stay owned by the caller and must outlive the pipeline.
  * Synchronous. */
 hh_status hh_pipeline_create(const hh_grid* grid, float K_gd, int64_t max_particles,
@@ -381,9 +384,10 @@ hh_status hh_pipeline_submit(hh_pipeline p, const float* xyzm_host, int64_t n,
  * frame two or more behind the last submitted one is complete. */
 hh_status hh_pipeline_wait(hh_pipeline p, uint64_t frame, int timeout_ms);
 
-/* The pipeline's volume (bookkeeping, no paper passage; owned by the pipeline, valid until
- * hh_pipeline_free); once frame t has been waited for and no later frame
- * submitted, it holds frame t's volume. */
+/* The volume of the last submitted frame's slot (bookkeeping, no paper
+ * passage; owned by the pipeline, valid until hh_pipeline_free): once that
+ * frame t has been waited for, it holds frame t's volume until frame t+2 is
+ * submitted. */
 hh_status hh_pipeline_volume(hh_pipeline p, hh_volume* vol);
 
 /* Waits (bounded, 60 s per frame) for the submitted frames and releases the

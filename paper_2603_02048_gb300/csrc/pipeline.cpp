@@ -3,15 +3,18 @@
 // is marched through it (Secs. 3.3.2-3.3.3), and the display images go back
 // to host memory.
 //
-// Frames alternate between two slots (device particle buffer, device image
-// buffers, events) and three streams: `up` copies a frame's particles to the
-// device, `comp` rebuilds the one shared volume and marches the views (so
-// frames are built and marched in order), `down` copies the images back. A
-// frame's upload waits only for the slot's previous user to be done, so the
-// upload of frame t+1 and the download of frame t-1 run on the copy engines
-// while frame t's kernels run. Submitting frame t first waits for frame t-2
-// (the slot's previous frame) to complete, which bounds the frames in flight
-// to two. All host waits are bounded.
+// Frames alternate between two slots, each with its own volume, device
+// particle buffer, image buffers, events and two compute streams: `up`
+// copies a frame's particles to the device, the slot's `build` stream
+// rebuilds the slot's volume, its `march` stream marches the views, `down`
+// copies the images back. With a volume per slot, frame t+1's splat and
+// field kernels run beside frame t's march; their stream has the device's
+// highest priority, so their blocks take the SMs as the march's blocks
+// retire (the build's memory-bound field pass fills the march's issue gaps)
+// instead of waiting for the whole march. The upload of frame t+1 and the
+// download of frame t-1 run on the copy engines meanwhile. Submitting frame t first waits for frame t-2 (the
+// slot's previous frame) to complete, which bounds the frames in flight to
+// two. All host waits are bounded.
 #include <algorithm>
 #include <chrono>
 #include <thread>
@@ -26,11 +29,14 @@ constexpr int kMaxViews = 4096;
 constexpr int kSubmitWaitMs = 60000;
 
 struct PipeSlot {
+    hh_volume vol = nullptr;         // this slot's frames' volume
+    cudaStream_t build = nullptr;    // rebuild of this slot's frames (highest priority)
+    cudaStream_t march = nullptr;    // march of this slot's frames
     float* parts_dev = nullptr;      // max_particles float4
     uint8_t* rgb8_dev = nullptr;     // every view's H*W*3 bytes, back to back
     std::vector<hh_view_out> outs;   // rgb8 pointers into rgb8_dev
     hh_batch batch = nullptr;        // the views as one launch (cfg given)
-    cudaEvent_t uploaded = nullptr, rendered = nullptr, downloaded = nullptr;
+    cudaEvent_t uploaded = nullptr, built = nullptr, rendered = nullptr, downloaded = nullptr;
     int64_t frame = -1;              // last frame submitted in this slot
 };
 
@@ -68,7 +74,6 @@ struct DeviceScope {
 }  // namespace
 
 struct hh_pipeline_s {
-    hh_volume vol = nullptr;
     float K = 0.0f;
     int64_t max_particles = 0;
     std::vector<hh_camera> cams;
@@ -76,7 +81,7 @@ struct hh_pipeline_s {
     hh_step_params params{};
     hh_background bg{};
     bool batched = false;
-    cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
+    cudaStream_t up = nullptr, down = nullptr;
     PipeSlot slot[kSlots];
     uint64_t next_frame = 0;
     int device = 0;
@@ -89,10 +94,12 @@ struct hh_pipeline_s {
             if (s.uploaded) cudaEventDestroy(s.uploaded);
             if (s.rendered) cudaEventDestroy(s.rendered);
             if (s.downloaded) cudaEventDestroy(s.downloaded);
+            if (s.built) cudaEventDestroy(s.built);
+            if (s.vol) hh_volume_free(s.vol);
+            if (s.build) cudaStreamDestroy(s.build);
+            if (s.march) cudaStreamDestroy(s.march);
         }
-        if (vol) hh_volume_free(vol);
         if (up) cudaStreamDestroy(up);
-        if (comp) cudaStreamDestroy(comp);
         if (down) cudaStreamDestroy(down);
     }
 };
@@ -131,23 +138,29 @@ hh_status hh_pipeline_create(const hh_grid* grid, float K_gd, int64_t max_partic
         total += (p->view_bytes.back() + 255) & ~size_t(255);
     }
     cudaError_t e = cudaSuccess;
-    for (cudaStream_t* s : {&p->up, &p->comp, &p->down})
+    for (cudaStream_t* s : {&p->up, &p->down, &p->slot[0].march, &p->slot[1].march})
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    for (PipeSlot& s : p->slot)
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithPriority(&s.build, cudaStreamNonBlocking, greatest);
     if (e != cudaSuccess) {
         delete p;
         return hh::cuda_fail(e, "pipeline streams");
     }
-    // the volume, built empty once (allocates it and its density scratch)
+    // the slots' volumes, built empty once (allocates them and their density scratch)
     const hh_particles none{nullptr, 0};
-    if ((st = hh_build_index_field(&none, grid, K_gd, p->comp, &p->vol)) != HH_OK) {
-        delete p;
-        return st;
-    }
+    for (PipeSlot& s : p->slot)
+        if ((st = hh_build_index_field(&none, grid, K_gd, s.build, &s.vol)) != HH_OK) {
+            delete p;
+            return st;
+        }
     for (PipeSlot& s : p->slot) {
         e = hh::dev_alloc(reinterpret_cast<void**>(&s.parts_dev),
                        static_cast<size_t>(std::max<int64_t>(max_particles, 1)) * 16);
         if (e == cudaSuccess) e = hh::dev_alloc(reinterpret_cast<void**>(&s.rgb8_dev), total);
-        for (cudaEvent_t* ev : {&s.uploaded, &s.rendered, &s.downloaded})
+        for (cudaEvent_t* ev : {&s.uploaded, &s.built, &s.rendered, &s.downloaded})
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e != cudaSuccess) {
             delete p;
@@ -161,7 +174,7 @@ hh_status hh_pipeline_create(const hh_grid* grid, float K_gd, int64_t max_partic
             off += (p->view_bytes[v] + 255) & ~size_t(255);
         }
         if (p->batched) {
-            if ((st = hh_batch_create(p->vol, cams, n_cams, params, bg, s.outs.data(),
+            if ((st = hh_batch_create(s.vol, cams, n_cams, params, bg, s.outs.data(),
                                       &s.batch)) != HH_OK ||
                 (st = hh_batch_set_config(s.batch, cfg)) != HH_OK) {
                 delete p;
@@ -169,8 +182,10 @@ hh_status hh_pipeline_create(const hh_grid* grid, float K_gd, int64_t max_partic
             }
         }
     }
-    e = cudaEventRecord(p->slot[0].rendered, p->comp);
-    if (e == cudaSuccess) e = wait_event(p->slot[0].rendered, kSubmitWaitMs);
+    for (PipeSlot& s : p->slot) {
+        if (e == cudaSuccess) e = cudaEventRecord(s.rendered, s.build);
+        if (e == cudaSuccess) e = wait_event(s.rendered, kSubmitWaitMs);
+    }
     if (e != cudaSuccess) {
         delete p;
         return e == cudaErrorNotReady ? fail(HH_ERR_TIMEOUT, "pipeline set-up timed out")
@@ -206,18 +221,22 @@ hh_status hh_pipeline_submit(hh_pipeline p, const float* xyzm_host, int64_t n,
         e = cudaMemcpyAsync(s.parts_dev, xyzm_host, static_cast<size_t>(n) * 16,
                             cudaMemcpyHostToDevice, p->up);
     if (e == cudaSuccess) e = cudaEventRecord(s.uploaded, p->up);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->comp, s.uploaded, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s.build, s.uploaded, 0);
     if (e != cudaSuccess) return hh::cuda_fail(e, "particle upload");
+    // the slot's previous march (frame t-2) is done: its images were downloaded
     const hh_particles parts{s.parts_dev, n};
-    hh_status st = hh_volume_rebuild(p->vol, &parts, p->K, p->comp);
+    hh_status st = hh_volume_rebuild(s.vol, &parts, p->K, s.build);
     if (st != HH_OK) return st;
+    e = cudaEventRecord(s.built, s.build);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s.march, s.built, 0);
+    if (e != cudaSuccess) return hh::cuda_fail(e, "volume build");
     if (p->batched)
-        st = hh_batch_launch_graph(s.batch, p->comp);
+        st = hh_batch_launch_graph(s.batch, s.march);
     else
-        st = hh_trace(p->vol, p->cams.data(), static_cast<int>(p->cams.size()), &p->params,
-                      &p->bg, s.outs.data(), p->comp);
+        st = hh_trace(s.vol, p->cams.data(), static_cast<int>(p->cams.size()), &p->params,
+                      &p->bg, s.outs.data(), s.march);
     if (st != HH_OK) return st;
-    e = cudaEventRecord(s.rendered, p->comp);
+    e = cudaEventRecord(s.rendered, s.march);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->down, s.rendered, 0);
     for (size_t v = 0; v < p->cams.size() && e == cudaSuccess; ++v)
         e = cudaMemcpyAsync(rgb8_host[v], s.outs[v].rgb8, p->view_bytes[v],
@@ -249,7 +268,8 @@ hh_status hh_pipeline_wait(hh_pipeline p, uint64_t frame, int timeout_ms) {
 
 hh_status hh_pipeline_volume(hh_pipeline p, hh_volume* vol) {
     if (!p || !vol) return hh::fail(HH_ERR_INVALID_ARG, "pipeline or output is NULL");
-    *vol = p->vol;
+    // the slot of the last submitted frame (slot 0 before any)
+    *vol = p->slot[p->next_frame == 0 ? 0 : (p->next_frame - 1) % kSlots].vol;
     return hh::ok();
 }
 

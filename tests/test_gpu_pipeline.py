@@ -63,19 +63,23 @@ def test_pipeline_frames_equal_trace(gpu, batched):
     cfg = {"block_threads": 128, "blocks_per_sm": 0, "refill_min": 32, "tile_w": 8}
     pipe = hh.hh_pipeline_create(hh.make_grid(DIMS, 2.0, "fp16"), f32(hi.K_GD), 6000, cams,
                                  params, bg_t, cfg if batched else None)
-    vol = hh.hh_pipeline_volume(pipe)
     # one frame at a time: each image against hh_trace on the frame's volume
+    # (the two slots' volumes alternate)
     serial = []
+    vols = set()
     for t, parts in enumerate(frames):
         imgs = [_pinned(torch, np.zeros(c["width"] * c["height"] * 3, np.uint8)) for c in cams]
         f = hh.hh_pipeline_submit(pipe, _pinned(torch, parts), imgs)
         assert f == t
         hh.hh_pipeline_wait(pipe, f)
+        vol = hh.hh_pipeline_volume(pipe)
+        vols.add(vol.handle.value)
         want = _trace_rgb8(hh, torch, vol, cams, params, bg_t)
         for a, b in zip(imgs, want):
             assert np.array_equal(a.numpy(), b)
         serial.append([a.numpy().copy() for a in imgs])
     assert any(not np.array_equal(serial[0][0], s[0]) for s in serial[1:])  # frames differ
+    assert len(vols) == 2  # one volume per slot
     # two frames in flight: the same images (the FP32 atomics of the splat may
     # change a last bit of the volume between builds: at most one display level)
     imgs = [[_pinned(torch, np.zeros(c["width"] * c["height"] * 3, np.uint8)) for c in cams]
