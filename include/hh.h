@@ -406,10 +406,11 @@ hh_status hh_pipeline_free(hh_pipeline p);
  * tiles of every admitted request from a device queue that a host thread
  * appends to while it runs, so a new request's rays start as soon as warps
  * free up, beside those of the requests already on the GPU (per-ray results
- * bit-identical to hh_trace). A request is admitted while fewer than
- * max_slots are on the GPU and its outputs fit in the server's device-memory
- * budget; requests that do not fit yet wait (later smaller ones may pass
- * them unless they have waited over 200 ms); a request whose outputs exceed
+ * bit-identical to hh_trace). Waiting requests are admitted smallest first
+ * (fewest rays), except that one waiting over 50 ms goes ahead of all younger
+ * ones, while fewer than max_slots are on the GPU and its outputs fit in the
+ * server's device-memory budget; requests that do not fit yet wait (others
+ * may pass them unless they have waited over 200 ms); a request whose outputs exceed
  * the whole budget is refused (HH_ERR_OOM); requests for a frame not yet put
  * wait for it. Requests with another step schedule, background or grid than
  * the running ones wait for those to finish. Every wait is bounded: the

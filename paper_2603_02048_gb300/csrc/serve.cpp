@@ -16,9 +16,11 @@
 // Requests share the worker's launch-wide arguments (grid dimensions,
 // storage, step schedule, background): a request of another schedule or
 // scene waits until the running ones are done, then the worker restarts with
-// its arguments. A request whose outputs exceed the whole budget is refused;
-// requests that do not fit yet wait (later ones may pass them unless they
-// have waited over 200 ms); requests for a frame not yet put wait for it. All
+// its arguments. Waiting requests are admitted smallest first (fewest rays),
+// except that a request waiting over kAgeMs goes ahead of all younger ones.
+// A request whose outputs exceed the whole budget is refused; requests that
+// do not fit yet wait (others may pass them unless they have waited over
+// 200 ms); requests for a frame not yet put wait for it. All
 // host waits are bounded, and so is every wait of the worker.
 #include <algorithm>
 #include <chrono>
@@ -40,6 +42,7 @@ constexpr int kMaxViews = 256;         // views per request
 constexpr int kMaxSlots = 64;          // requests on the GPU at once
 constexpr int kJobs = 1 << 14;         // job entries between queue resets
 constexpr int kViewRecords = 1 << 16;  // view records between queue resets
+constexpr double kAgeMs = 50.0;  // admission: a request waiting this long goes first
 constexpr unsigned long long kIdleNs = 2000000;   // a worker warp leaves after 2 ms without work
 constexpr unsigned long long kEntryNs = 5000000;  // a published entry missing for 5 ms fails its job
 
@@ -60,6 +63,7 @@ struct Request {
     hh_background bg{};
     int outputs = HH_OUT_RGB;
     size_t bytes = 0;   // output bytes in the pool
+    uint64_t rays = 0;  // primary rays of all its views
     size_t offset = 0;  // pool offset once admitted
     bool has_memory = false;
     std::vector<hh_view_out> outs;
@@ -396,6 +400,16 @@ void hh_server_s::reset_queue() {
 
 void hh_server_s::admit() {
     const double t = now_ms();
+    // smallest request first, except that a request waiting longer than
+    // kAgeMs goes ahead of every younger one (oldest first among them)
+    std::stable_sort(pending.begin(), pending.end(), [&](uint64_t a, uint64_t b) {
+        auto ia = reqs.find(a), ib = reqs.find(b);
+        if (ia == reqs.end() || ib == reqs.end()) return ia != reqs.end() && ib == reqs.end();
+        const bool oa = t - ia->second.t_submit > kAgeMs, ob = t - ib->second.t_submit > kAgeMs;
+        if (oa != ob) return oa;
+        if (oa) return ia->second.t_submit < ib->second.t_submit;
+        return ia->second.rays < ib->second.rays;
+    });
     for (auto it = pending.begin(); it != pending.end();) {
         auto rit = reqs.find(*it);
         if (rit == reqs.end()) {  // released or cancelled while waiting
@@ -620,6 +634,7 @@ hh_status hh_serve_submit(hh_server S, int64_t frame_id, const hh_camera* cams, 
     for (int i = 0; i < n_views; ++i) {
         if ((st = hh::check_camera(cams[i], i)) != HH_OK) return st;
         r.bytes += view_bytes(cams[i], outputs);
+        r.rays += static_cast<uint64_t>(cams[i].width) * cams[i].height;
     }
     std::lock_guard<std::mutex> lock(S->mu);
     if (S->pool.footprint(r.bytes) > S->pool.capacity()) {
