@@ -176,6 +176,26 @@ __device__ __forceinline__ void axis_cell(float u, int n, int& i0, float& f) {
 __device__ __forceinline__ float4 ld_fp32(const float4* __restrict__ v, unsigned i) {
     return __ldg(v + i);
 }
+// x-lerp of two FP16 corners read raw (four halves each), in FP32: the first
+// corner converted, the second converted inside the subtraction
+// (sub.rn.f32.f16: one rounding, as converting first and subtracting in FP32),
+// then a + t (b - a) on both channel pairs.
+__device__ __forceinline__ float4 xlerp_fp16(uint2 a, uint2 b, float2 tt) {
+    const float2 a0 = __half22float2(*reinterpret_cast<const __half2*>(&a.x));
+    const float2 a1 = __half22float2(*reinterpret_cast<const __half2*>(&a.y));
+    float2 d0, d1;
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "sub.rn.f32.f16 %0, l, %3;\n\tsub.rn.f32.f16 %1, h, %4;\n\t}"
+        : "=f"(d0.x), "=f"(d0.y)
+        : "r"(b.x), "f"(a0.x), "f"(a0.y));
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "sub.rn.f32.f16 %0, l, %3;\n\tsub.rn.f32.f16 %1, h, %4;\n\t}"
+        : "=f"(d1.x), "=f"(d1.y)
+        : "r"(b.y), "f"(a1.x), "f"(a1.y));
+    const float2 lo = fma2(tt, d0, a0), hi = fma2(tt, d1, a1);
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 __device__ __forceinline__ float4 ld_fp16(const ushort4* __restrict__ v, unsigned i) {
     const uint2 raw = __ldg(reinterpret_cast<const uint2*>(v) + i);
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
@@ -185,7 +205,7 @@ __device__ __forceinline__ float4 ld_fp16(const ushort4* __restrict__ v, unsigne
 
 // Trilinear sample of {dn, g} at lattice coordinate u = position + 1/2
 // (Sec. 3.3.1: n and grad n sampled with trilinear interpolation); FP16
-// volumes are interpolated as stored and scaled once afterwards.
+// volumes are interpolated as stored (code units, value / scale).
 // With HH_DEBUG_BOUNDS the corner indices are checked against the padded
 // axes (ix in [0, nx], so that ix + 1 <= nx + 1): a corner outside is counted
 // in g_bounds_violations, flagged on the ray (HH_FLAG_CLAMP in `flags`) and
@@ -196,7 +216,7 @@ __device__ unsigned long long g_bounds_violations;
 
 template <int STORAGE, bool CLAMP>
 __device__ __forceinline__ Sample fetch(const VolArgs& A, const void* __restrict__ vol, float3 u,
-                                        float s_n, float s_g, uint32_t& flags) {
+                                        uint32_t& flags) {
     int ix, iy, iz;
     float fx, fy, fz;
     axis_cell<CLAMP>(u.x, A.nx, ix, fx);
@@ -236,25 +256,21 @@ __device__ __forceinline__ Sample fetch(const VolArgs& A, const void* __restrict
         v101 = ld_fp32(V, b001 + dx);
         v011 = ld_fp32(V, b011);
         v111 = ld_fp32(V, b011 + dx);
-    } else {
-        const ushort4* V = static_cast<const ushort4*>(vol);
-        v000 = ld_fp16(V, b);
-        v100 = ld_fp16(V, b + dx);
-        v010 = ld_fp16(V, b010);
-        v110 = ld_fp16(V, b010 + dx);
-        v001 = ld_fp16(V, b001);
-        v101 = ld_fp16(V, b001 + dx);
-        v011 = ld_fp16(V, b011);
-        v111 = ld_fp16(V, b011 + dx);
     }
     float4 c;
     if (STORAGE == HH_STORE_FP16_SCALED) {
-    // FP16 storage: lerps along x, then y, then z with packed FP32x2
-    // arithmetic, two channels per instruction (measured 8 % faster there;
-    // on FP32 storage the 8-weight form below is faster)
+    // FP16 storage: lerps along x (the second corner converted inside the
+    // subtraction), then y, then z with packed FP32x2 arithmetic, two channels
+    // per instruction (measured 8 % faster there; on FP32 storage the 8-weight
+    // form below is faster)
+    const uint2* V = static_cast<const uint2*>(vol);
+    const uint2 r000 = __ldg(V + b), r100 = __ldg(V + b + dx);
+    const uint2 r010 = __ldg(V + b010), r110 = __ldg(V + b010 + dx);
+    const uint2 r001 = __ldg(V + b001), r101 = __ldg(V + b001 + dx);
+    const uint2 r011 = __ldg(V + b011), r111 = __ldg(V + b011 + dx);
     const float2 tx = make_float2(fx, fx), ty = make_float2(fy, fy), tz = make_float2(fz, fz);
-    c = lerp4x2(lerp4x2(lerp4x2(v000, v100, tx), lerp4x2(v010, v110, tx), ty),
-                lerp4x2(lerp4x2(v001, v101, tx), lerp4x2(v011, v111, tx), ty), tz);
+    c = lerp4x2(lerp4x2(xlerp_fp16(r000, r100, tx), xlerp_fp16(r010, r110, tx), ty),
+                lerp4x2(xlerp_fp16(r001, r101, tx), xlerp_fp16(r011, r111, tx), ty), tz);
     } else {
     // the standard 8-corner weights
     const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
@@ -279,18 +295,14 @@ __device__ __forceinline__ Sample fetch(const VolArgs& A, const void* __restrict
     HH_ACC(w111, v111)
 #undef HH_ACC
     }
+    // FP16 storage: the sample stays in code units (value / scale); the
+    // power-of-two scales are applied downstream, where a product by them is
+    // exact, so the result equals scaling here (see perp_rate)
     Sample s;
-    if (STORAGE == HH_STORE_FP32) {
-        s.dn = c.x;
-        s.gx = c.y;
-        s.gy = c.z;
-        s.gz = c.w;
-    } else {
-        s.dn = c.x * s_n;
-        s.gx = c.y * s_g;
-        s.gy = c.z * s_g;
-        s.gz = c.w * s_g;
-    }
+    s.dn = c.x;
+    s.gx = c.y;
+    s.gy = c.z;
+    s.gz = c.w;
     return s;
 }
 
@@ -464,15 +476,22 @@ __device__ __forceinline__ float exit_fraction(const VolArgs& A, float3 hi, floa
     return fmaxf(tau, 0.0f);
 }
 
+// n and the transverse gradient g_perp = (I - w w^T) g at u (Eq. 15), with
+// |g_perp|. With FP16 storage g_perp is returned in code units, g_perp / s_g:
+// the caller multiplies the scalar that scales it by s_g (gsc in ray_step). s_n
+// and s_g are powers of two, so every such product is exact and the results
+// equal those of scaling the sample first: n = 1 + dn s_n is one rounding
+// either way, and |g_perp| = s_g |g_perp / s_g| exactly.
 template <int STORAGE, bool CLAMP>
 __device__ __forceinline__ float3 perp_rate(const VolArgs& A, const void* __restrict__ vol,
                                             float3 u, float3 w, float s_n, float s_g, float& n,
                                             float& gperp_norm, uint32_t& flags) {
-    const Sample s = fetch<STORAGE, CLAMP>(A, vol, u, s_n, s_g, flags);
-    n = 1.0f + s.dn;
+    const Sample s = fetch<STORAGE, CLAMP>(A, vol, u, flags);
+    n = STORAGE == HH_STORE_FP32 ? 1.0f + s.dn : fmaf(s.dn, s_n, 1.0f);
     const float3 g = make_float3(s.gx, s.gy, s.gz);
     const float3 gp = fma3(-dot(w, g), w, g);
     gperp_norm = sqrt_approx(dot(gp, gp));
+    if (STORAGE != HH_STORE_FP32) gperp_norm *= s_g;
     return gp;
 }
 
@@ -539,28 +558,29 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, const void* __restric
     const float3 C = R.c;
     float ds;
     float3 dnew, inc;
+    const float gsc = STORAGE == HH_STORE_FP32 ? 1.0f : R.sg;  // see perp_rate
     if (STEPPER == HH_STEP_RK4) {
         float n1, gpn, n2, n3, n4, unused;
         const float3 w1 = wr + d;
         const float3 gp1 = perp_rate<STORAGE, true>(V, vol, C, w1, R.sn, R.sg, n1, gpn, R.flags);
         ds = step_length<ADAPTIVE>(V, n1, gpn);
         const float hds = 0.5f * ds;
-        const float3 k1 = __fdividef(1.0f, n1) * gp1;
+        const float3 k1 = (__fdividef(1.0f, n1) * gsc) * gp1;
         const float3 d2 = fma3(hds, k1, d);
         const float3 w2 = wr + d2;
         const float3 gp2 = perp_rate<STORAGE, true>(V, vol, fma3(hds, w1, C), w2, R.sn, R.sg, n2,
                                                     unused, R.flags);
-        const float3 k2 = __fdividef(1.0f, n2) * gp2;
+        const float3 k2 = (__fdividef(1.0f, n2) * gsc) * gp2;
         const float3 d3 = fma3(hds, k2, d);
         const float3 w3 = wr + d3;
         const float3 gp3 = perp_rate<STORAGE, true>(V, vol, fma3(hds, w2, C), w3, R.sn, R.sg, n3,
                                                     unused, R.flags);
-        const float3 k3 = __fdividef(1.0f, n3) * gp3;
+        const float3 k3 = (__fdividef(1.0f, n3) * gsc) * gp3;
         const float3 d4 = fma3(ds, k3, d);
         const float3 w4 = wr + d4;
         const float3 gp4 = perp_rate<STORAGE, true>(V, vol, fma3(ds, w3, C), w4, R.sn, R.sg, n4,
                                                     unused, R.flags);
-        const float3 k4 = __fdividef(1.0f, n4) * gp4;
+        const float3 k4 = (__fdividef(1.0f, n4) * gsc) * gp4;
         const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
         const float3 dsum = fma3(ds * (1.0f / 6.0f), ksum, d);
         dnew = renormalize(wr + dsum, dsum);
@@ -571,7 +591,7 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, const void* __restric
         const float3 w = wr + d;
         const float3 gp = perp_rate<STORAGE, false>(V, vol, C, w, R.sn, R.sg, n, gpn, R.flags);
         ds = step_length<ADAPTIVE>(V, n, gpn);
-        const float3 d1 = fma3(__fdividef(ds, n), gp, d);
+        const float3 d1 = fma3(__fdividef(ds, n) * gsc, gp, d);
         // Eq. 16: w' = normalize(w1), C' = C + ds w'; with w' = (1 + r) w1
         // the increment is ds (1 + r) w1 (w' itself is formed only at the exit)
         const float3 w1 = wr + d1;
