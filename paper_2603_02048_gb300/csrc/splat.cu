@@ -2,21 +2,22 @@
 // rho(x_v) = sum_p m_p W(|x_v - x_p|, h) at voxel centres, W the M4 cubic
 // spline with support 2h.
 //
-// Four particles per warp, eight lanes each. A lane owns an (x, y) column of
-// its particle's footprint (the voxels whose centres lie within 2h on every
-// axis: 8^3 for h = 2), the eight lanes covering a row of 8 columns per pass,
-// and walks the column in z with the column's squared distance computed
-// once; at every z slice a warp's atomics cover four 8-float rows (four
-// 32-byte sectors, one per particle) and compile to fire-and-forget
-// reductions in L2. The per-particle set-up (footprint bounds, kernel
-// coefficients) is shared by the four particles' lanes: against one particle
-// per warp (lanes 8 x 4 over the footprint) this takes 12 % off the build,
-// while eight per warp (half-sector reductions) is slower again. Columns
-// and voxels beyond the support (r^2 >= 4h^2, about half of the footprint
-// box) skip the atomic; indices are 32-bit (grids hold fewer than 2^31
-// voxels). The kernel is evaluated in r with the particle's mass folded into
-// its coefficients, and a column of exactly 8 voxels (every interior
-// particle when h = 2) is walked fully unrolled.
+// Two kernels: splat_box8_kernel for supports of at most 8 voxels per axis
+// (2h <= 4, the paper's h = 2), described where it is defined, and
+// splat_warp_kernel for wider ones. Both put four particles on a warp,
+// eight lanes each, so that a warp's reductions at one (y, z) row cover four
+// 8-float runs (four 32-byte sectors, one per particle) and compile to
+// fire-and-forget reductions in L2, and the per-particle set-up is shared by
+// the four particles' lanes (against one particle per warp this took 12 %
+// off the build; eight per warp, half-sector reductions, was slower again).
+//
+// splat_warp_kernel: a lane owns an (x, y) column of its particle's
+// footprint (the voxels whose centres lie within 2h on every axis), the
+// eight lanes covering a row of 8 columns per pass, and walks the column in z
+// with the column's squared distance computed once. Columns and voxels
+// beyond the support (r^2 >= 4h^2) skip the atomic; indices are 32-bit
+// (grids hold fewer than 2^31 voxels). The kernel is evaluated in r with the
+// particle's mass folded into its coefficients.
 #include <algorithm>
 
 #include "hh_internal.h"
@@ -105,20 +106,108 @@ __global__ void __launch_bounds__(256) splat_warp_kernel(const float4* __restric
             if (!(dxy2 < reach2)) continue;  // the whole column is outside the support
             unsigned v = (static_cast<unsigned>(z0) * static_cast<unsigned>(ny) +
                           static_cast<unsigned>(j)) * static_cast<unsigned>(nx) + i;
-            if (ez == 8) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k, v += plane) {
-                    const float dz = dz0 + static_cast<float>(k);  // exact at these magnitudes
-                    const float r2 = fmaf(dz, dz, dxy2);
-                    if (r2 < reach2) atomicAdd(rho + v, m4_mass(cf, r2, sqrt_approx(r2)));
-                }
-            } else {
-                float dz = dz0;  // (k + 1/2) - z exactly: each +1 is exact at these magnitudes
-                for (int k = 0; k < ez; ++k, dz += 1.0f, v += plane) {
-                    const float r2 = fmaf(dz, dz, dxy2);
-                    if (r2 < reach2) atomicAdd(rho + v, m4_mass(cf, r2, sqrt_approx(r2)));
-                }
+            float dz = dz0;  // (k + 1/2) - z exactly: each +1 is exact at these magnitudes
+            for (int k = 0; k < ez; ++k, dz += 1.0f, v += plane) {
+                const float r2 = fmaf(dz, dz, dxy2);
+                if (r2 < reach2) atomicAdd(rho + v, m4_mass(cf, r2, sqrt_approx(r2)));
             }
+        }
+    }
+}
+
+// Adds v to the float at byte address addr when t > 0 (a predicated
+// reduction: no branch, nothing issued to memory otherwise).
+__device__ __forceinline__ void red_add_if_positive(float t, uint64_t addr, float v) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.gt.f32 p, %0, 0f00000000;\n\t"
+                 "@p red.global.add.f32 [%1], %2;\n\t}"
+                 :: "f"(t), "l"(addr), "f"(v) : "memory");
+}
+
+// PTX sqrt.approx.ftz.f32: a subnormal r^2 is taken as 0 (r ~ 0 there,
+// where W is flat), which keeps the instruction free of a subnormal path.
+__device__ __forceinline__ float sqrt_approx_ftz(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// a * b + c with a 32 x 32 -> 64-bit product (PTX mad.wide.u32).
+__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+    uint64_t r;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(a), "r"(b), "l"(c));
+    return r;
+}
+
+// First of the 8 voxel slots along one axis that cover every voxel centre
+// within `reach` (<= 4) of x: the smallest k with k + 1/2 > x - reach,
+// clamped to [-8, n] so that the slots' indices stay small (slots outside
+// [0, n) are masked by their distance; NaN converts to 0 and is masked the
+// same way).
+__device__ __forceinline__ int box8_start(float x, float reach, int n) {
+    const float a = fminf(fmaxf(x - reach - 0.5f, -9.0f), static_cast<float>(n));
+    return __float2int_rd(a) + 1;
+}
+
+// Distance from x to the centre of voxel k, infinite when k lies outside
+// [0, n).
+__device__ __forceinline__ float dist_or_inf(int k, int n, float x) {
+    return (k >= 0 && k < n) ? (static_cast<float>(k) + 0.5f) - x : __int_as_float(0x7f800000);
+}
+
+// The splat for kernel radii 2h <= 4 voxels (the paper's h = 2 among them):
+// every particle's support fits an 8 x 8 x 8 box of voxel slots. Four
+// particles per warp, eight lanes each on the box's x slots; a lane walks its
+// 8 y rows and 8 z slots fully unrolled. Slots outside the grid get an
+// infinite distance, so no index test is needed per slot, and a slot adds
+// its mass only where it lies inside the support (a predicated reduction, no
+// branch). The kernel is evaluated in the branch-free form
+// m W = m norm (2 t^3 - u^3), t = 1 - r/2h, u = max(1 - r/h, 0), equal to the
+// two-piece M4 on [0, 2h): 2 t^3 = (2 - q)^3 / 4 and u^3 = (1 - q)^3 for
+// q = r/h < 1. Against splat_warp_kernel (per-column and per-voxel branches,
+// the footprint walked in loops) this issues a third fewer instructions and
+// the 256^3 plume's splat drops from 120 to 91 us; packed FP32x2 arithmetic
+// for slot pairs issues fewer still but is no faster, the L2 reductions now
+// setting the pace.
+template <int PPW>
+__global__ void __launch_bounds__(256) splat_box8_kernel(const float4* __restrict__ parts,
+                                                         int64_t n, int nx, int ny, int nz,
+                                                         float reach, float inv_2h, float inv_h,
+                                                         float norm, float* __restrict__ rho) {
+    constexpr int LPP = 32 / PPW;
+    static_assert(LPP == 8, "eight lanes per particle: one per x slot");
+    const int lane = threadIdx.x & 31;
+    const int64_t p =
+        ((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * PPW + lane / LPP;
+    if (p >= n) return;
+    const float4 q = __ldg(parts + p);
+    const int sx = box8_start(q.x, reach, nx), sy = box8_start(q.y, reach, ny),
+              sz = box8_start(q.z, reach, nz);
+    const int i = sx + (lane % LPP);
+    const float dx = dist_or_inf(i, nx, q.x);
+    const float dx2 = dx * dx;
+    float dz[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dz[k] = dist_or_inf(sz + k, nz, q.z);
+    const float mn = q.w * norm, c_t = 2.0f * mn, c_u = -mn;
+    const uint64_t row_b = static_cast<uint64_t>(nx) * sizeof(float);
+    // a plane is at most 16384^2 floats (1 GiB): its byte size fits 32 bits
+    const uint32_t plane_b = static_cast<uint32_t>(row_b * static_cast<uint64_t>(ny));
+    // byte address of slot (i, sy, sz); unsigned arithmetic, formed for
+    // masked slots too but never dereferenced there
+    uint64_t row = reinterpret_cast<uint64_t>(rho) +
+                   static_cast<uint64_t>((static_cast<int64_t>(sz) * ny + sy) * nx + i) *
+                       sizeof(float);
+#pragma unroll
+    for (int j = 0; j < 8; ++j, row += row_b) {
+        const float dy = dist_or_inf(sy + j, ny, q.y);
+        const float dxy2 = fmaf(dy, dy, dx2);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float r = sqrt_approx_ftz(fmaf(dz[k], dz[k], dxy2));
+            const float t = fmaf(r, -inv_2h, 1.0f);
+            const float u = __saturatef(fmaf(r, -inv_h, 1.0f));
+            const float w = fmaf(t * t * t, c_t, (u * u * u) * c_u);
+            red_add_if_positive(t, mad_wide(plane_b, k, row), w);
         }
     }
 }
@@ -274,8 +363,13 @@ cudaError_t launch_splat(const float4* xyzm, int64_t n, int nx, int ny, int nz, 
     const int64_t blocks = (warps * 32 + threads - 1) / threads;
     const double hd = h;
     const float norm = static_cast<float>(1.0 / (3.14159265358979323846 * hd * hd * hd));
-    splat_warp_kernel<kParticlesPerWarp><<<static_cast<unsigned>(blocks), threads, 0, s>>>(
-        xyzm, n, nx, ny, nz, h, static_cast<float>(1.0 / hd), norm, rho);
+    if (2.0 * hd <= 4.0)
+        splat_box8_kernel<kParticlesPerWarp><<<static_cast<unsigned>(blocks), threads, 0, s>>>(
+            xyzm, n, nx, ny, nz, 2.0f * h, static_cast<float>(0.5 / hd),
+            static_cast<float>(1.0 / hd), norm, rho);
+    else
+        splat_warp_kernel<kParticlesPerWarp><<<static_cast<unsigned>(blocks), threads, 0, s>>>(
+            xyzm, n, nx, ny, nz, h, static_cast<float>(1.0 / hd), norm, rho);
     count_launch();
     return cudaGetLastError();
 }

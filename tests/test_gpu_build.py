@@ -34,6 +34,8 @@ def _splat_gpu(hh, torch, parts, dims, h):
     ((64, 64, 64), 20000, 2.0, 4.0),   # interior plume-like load
     ((20, 17, 9), 500, 1.3, 0.0),      # non-integer support radius
     ((8, 8, 8), 1, 3.0, 0.0),          # one particle, support larger than the grid
+    ((3, 5, 7), 400, 2.0, -3.0),       # grid thinner than the support on every axis
+    ((2, 2, 2), 50, 2.0, -2.0),        # smallest grid
 ])
 def test_splat_matches_oracle(gpu, oracle_lib, dims, n, h, margin):
     hh, torch = gpu
@@ -42,6 +44,24 @@ def test_splat_matches_oracle(gpu, oracle_lib, dims, n, h, margin):
     want = oracle_lib.splat(parts, dims, h)
     # FP32 kernel values and FP32 atomic accumulation in arbitrary order
     assert np.abs(got - want).max() <= 1e-5 * want.max() + 1e-30
+
+
+@pytest.mark.parametrize("h", [2.0, 1.75])
+def test_splat_support_boundaries(gpu, oracle_lib, h):
+    """Particles whose support ends exactly on voxel centres (x - 2h - 1/2 an
+    integer), on voxel centres and on cell corners, inside and at the faces."""
+    hh, torch = gpu
+    dims = (19, 16, 13)
+    axis = np.concatenate([np.arange(-1, 20) + 0.5, np.arange(-1, 20) * 1.0,
+                           np.arange(0, 20) + 0.5 + 2 * h - np.floor(2 * h)])
+    rng = np.random.default_rng(11)
+    pos = rng.choice(axis, size=(600, 3))
+    pos[:, 1] %= 17.0
+    pos[:, 2] %= 14.0
+    parts = np.concatenate([pos, rng.uniform(0.5, 2.0, (600, 1))], axis=1).astype(np.float32)
+    got = _splat_gpu(hh, torch, parts, dims, h)
+    want = oracle_lib.splat(parts, dims, h)
+    assert np.abs(got - want).max() <= 1e-5 * want.max()
 
 
 def test_splat_plume_scene(gpu, oracle_lib):
