@@ -285,9 +285,13 @@ typedef struct {
                           row by row; 1 = the tiles of all views interleaved
                           by their relative row, so every view sweeps the
                           volume top to bottom at once (views at similar
-                          elevations then share the bricks in L2: 10 % less
-                          DRAM traffic on the 512^3 32-view batch). The
-                          render server's per-request launches use 0.     */
+                          elevations then share the bricks in L2: 17 % less
+                          DRAM traffic on the 512^3 32-view batch).       */
+    int tile_group;    /* 0 = each warp takes its own next tile; 1 = a block
+                          takes one tile per warp at once (consecutive tiles,
+                          neighbours in a view) so that its warps march them
+                          side by side on one SM and share its L1, with a
+                          barrier between groups; needs refill_min 32       */
 } hh_batch_config;
 
 /* Creates a batch of n_cams views (1..4096) over `vol` (the multi-camera
@@ -296,7 +300,7 @@ typedef struct {
  * table (and, for tile_order 1, the tile order) to the device (cudaMalloc +
  * synchronous copy); the volume, the background and the output buffers stay
  * owned by the caller and must outlive the batch. Default configuration:
- * {128, 0, 32, 8, 0}. */
+ * {128, 0, 32, 8, 0, 0}. */
 hh_status hh_batch_create(hh_volume vol, const hh_camera* cams, int n_cams,
                           const hh_step_params* params, const hh_background* bg,
                           const hh_view_out* outs, hh_batch* out);
@@ -312,7 +316,8 @@ hh_status hh_batch_get_config(hh_batch b, hh_batch_config* cfg);
 /* Autotuner (a GPU scheduling search; no paper passage). Times candidate
  * configurations (tile 8x4 / 4x8 / 16x2; 64, 128, 256 threads;
  * compaction at 32, 16, 8 idle lanes; full or half occupancy; views one
- * after the other or interleaved: 108 in all) with CUDA events
+ * after the other or interleaved; without compaction, warps or blocks taking
+ * tiles: 144 in all) with CUDA events
  * on `stream`, each as the median of |reps| launches, and keeps the fastest.
  * Results are cached in the process by workload (grid, storage, schedule,
  * view resolutions); reps > 0 reuses a cached result, reps < 0 re-measures.
@@ -446,7 +451,8 @@ typedef struct {
 hh_status hh_serve_create(size_t mem_budget_bytes, int max_slots, hh_server* out);
 
 /* Launch shape of the worker (block_threads, blocks_per_sm, tile_w of
- * hh_batch_config; refill_min and tile_order do not apply; a GPU scheduling
+ * hh_batch_config; refill_min, tile_order and tile_group do not apply (they
+ * are checked for range only); a GPU scheduling
  * choice, no paper passage). Waits (up to 60 s, else HH_ERR_BUSY) until no
  * request is waiting or running. HH_ERR_INVALID_ARG for a shape out of
  * range. */

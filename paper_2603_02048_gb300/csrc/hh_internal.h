@@ -103,16 +103,12 @@ cudaError_t launch_field(const float* rho, int nx, int ny, int nz, float K, hh_v
 
 cudaError_t launch_export(const hh_volume_s* vol, float4* dst, cudaStream_t s);
 
-// Batched launches with a caller-managed device view table (the server's
-// slots): build_view_table fills n records of view_record_bytes() each in host
-// memory for tile width tile_w and returns the total tile count (-1 if too
-// many); launch_batch resets `counter` and launches the persistent kernel.
+// View records for a caller-managed device view table (the server's jobs):
+// build_view_table fills n records of view_record_bytes() each in host memory
+// for tile width tile_w and returns the total tile count (-1 if too many).
 size_t view_record_bytes();
 int build_view_table(const hh_camera* cams, const hh_view_out* outs, int n, int tile_w,
                      void* host_records);
-cudaError_t launch_batch(const hh_volume_s* vol, const hh_step_params& P, const hh_background& bg,
-                         const void* views_dev, int n_views, int total_tiles, unsigned* counter,
-                         const hh_batch_config& cfg, int sm_count, cudaStream_t s);
 
 // The render server's persistent worker (ray-level continuous batching).
 // The host publishes requests ("jobs") into a device queue while the worker

@@ -719,13 +719,17 @@ __device__ __forceinline__ void tile_of(int t, int n_views, const int* s_begin,
 // current tile (and of the next tile when it runs out) while the other lanes
 // keep marching; refill_min = 32 refills only when every lane is idle, i.e.
 // plain tile-at-a-time scheduling, compiled separately (REFILL = false) as
-// march_kernel's loop around a tile counter. The per-ray arithmetic is
-// march_kernel's.
+// march_kernel's loop around a tile counter. In that mode `group` = 1 makes
+// the block, not the warp, the unit of scheduling: one atomic fetches one
+// tile per warp (consecutive tiles: neighbours in a view), the block's warps
+// march them side by side on one SM, sharing its L1, and meet at a barrier
+// before the next group, as march_kernel's blocks do when they retire. The
+// per-ray arithmetic is march_kernel's.
 template <int STORAGE, int STEPPER, bool ADAPTIVE, bool REFILL>
 __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_MIN_BLOCKS)
     march_batch_kernel(const VolArgs V, const ViewArgs* __restrict__ views, int n_views,
                        int total_tiles, int tile_w, unsigned* __restrict__ counter,
-                       int refill_min, const uint2* __restrict__ order) {
+                       int refill_min, const uint2* __restrict__ order, int group) {
     extern __shared__ int s_begin[];  // first tile of each view, then total_tiles
     for (int i = threadIdx.x; i <= n_views; i += blockDim.x)
         s_begin[i] = i < n_views ? views[i].tile_begin : total_tiles;
@@ -735,13 +739,25 @@ __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_M
     const unsigned lt_mask = (1u << lane) - 1u;
     const int tile_w_log2 = tile_w == 16 ? 4 : (tile_w == 8 ? 3 : 2);
     if (!REFILL) {
+        __shared__ int s_group;  // first tile of the block's current group
+        const int warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
         int lx, ly;
         tile_pixel(lane, tile_w_log2, lx, ly);
         for (;;) {
             int t = 0;
-            if (lane == 0) t = static_cast<int>(atomicAdd(counter, 1u));
-            t = __shfl_sync(FULL, t, 0);
-            if (t >= total_tiles) return;
+            if (group) {  // block-uniform branch
+                if (threadIdx.x == 0) s_group = static_cast<int>(atomicAdd(counter, 1u)) * warps;
+                __syncthreads();
+                const int g0 = s_group;
+                __syncthreads();  // read by every warp before thread 0 writes it again
+                if (g0 >= total_tiles) return;
+                t = g0 + warp;
+                if (t >= total_tiles) continue;
+            } else {
+                if (lane == 0) t = static_cast<int>(atomicAdd(counter, 1u));
+                t = __shfl_sync(FULL, t, 0);
+                if (t >= total_tiles) return;
+            }
             int lo, local;
             tile_of(t, n_views, s_begin, order, lo, local);
             const ViewArgs& C = views[lo];
@@ -1054,15 +1070,15 @@ struct SingleLaunch {
 template <int ST, int SP, bool AD>
 struct BatchLaunch {
     static void run(const VolArgs& V, const ViewArgs* views, int n_views, int total_tiles,
-                    int tile_w, unsigned* counter, int refill_min, const uint2* order, int blocks,
-                    int threads, cudaStream_t s) {
+                    int tile_w, unsigned* counter, int refill_min, const uint2* order, int group,
+                    int blocks, int threads, cudaStream_t s) {
         const size_t smem = (n_views + 1) * sizeof(int);
         if (refill_min >= 32)
             march_batch_kernel<ST, SP, AD, false><<<blocks, threads, smem, s>>>(
-                V, views, n_views, total_tiles, tile_w, counter, refill_min, order);
+                V, views, n_views, total_tiles, tile_w, counter, refill_min, order, group);
         else
             march_batch_kernel<ST, SP, AD, true><<<blocks, threads, smem, s>>>(
-                V, views, n_views, total_tiles, tile_w, counter, refill_min, order);
+                V, views, n_views, total_tiles, tile_w, counter, refill_min, order, 0);
     }
 };
 
@@ -1203,27 +1219,6 @@ int build_view_table(const hh_camera* cams, const hh_view_out* outs, int n, int 
     return static_cast<int>(tiles);
 }
 
-cudaError_t launch_batch(const hh_volume_s* vol, const hh_step_params& P, const hh_background& bg,
-                         const void* views_dev, int n_views, int total_tiles, unsigned* counter,
-                         const hh_batch_config& cfg, int sm_count, cudaStream_t s) {
-    if (vol->layout != HH_LAYOUT_BRICK2) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    int bps = cfg.blocks_per_sm;
-    if (bps <= 0) {
-        dispatch<BatchOccupancy>(vol->storage, P.stepper, P.adaptive, cfg.block_threads,
-                                 (n_views + 1) * sizeof(int), cfg.refill_min, &bps);
-        bps = max(bps, 1);
-    }
-    const VolArgs V = make_vol_args(vol, P, bg);
-    dispatch<BatchLaunch>(vol->storage, P.stepper, P.adaptive, V,
-                          static_cast<const ViewArgs*>(views_dev), n_views, total_tiles,
-                          cfg.tile_w, counter, cfg.refill_min, static_cast<const uint2*>(nullptr),
-                          sm_count * bps, cfg.block_threads, s);
-    count_launch();
-    return cudaGetLastError();
-}
-
 int serve_worker_blocks_per_sm(int storage, int stepper, int adaptive, int threads) {
     int bps = 0;
     dispatch<WorkerOccupancy>(storage, stepper, adaptive, threads, &bps);
@@ -1339,6 +1334,10 @@ hh_status check_config(const hh_batch_config* c) {
         return fail(HH_ERR_INVALID_ARG, "tile_w must be 4, 8 or 16");
     if (c->tile_order != 0 && c->tile_order != 1)
         return fail(HH_ERR_INVALID_ARG, "tile_order must be 0 or 1");
+    if (c->tile_group != 0 && c->tile_group != 1)
+        return fail(HH_ERR_INVALID_ARG, "tile_group must be 0 or 1");
+    if (c->tile_group == 1 && c->refill_min != 32)
+        return fail(HH_ERR_INVALID_ARG, "tile_group 1 needs tile-at-a-time scheduling (refill_min 32)");
     return HH_OK;
 }
 
@@ -1367,7 +1366,8 @@ cudaError_t enqueue(hh_batch b, int blocks, cudaStream_t s) {
     hh::dispatch<hh::BatchLaunch>(b->vol->storage, b->params.stepper, b->params.adaptive, V,
                                   b->views_dev, static_cast<int>(b->cams.size()), b->total_tiles,
                                   b->cfg.tile_w, b->counter_dev, b->cfg.refill_min,
-                                  static_cast<const uint2*>(b->order_dev), blocks, threads, s);
+                                  static_cast<const uint2*>(b->order_dev), b->cfg.tile_group,
+                                  blocks, threads, s);
     hh::count_launch();
     return cudaGetLastError();
 }
@@ -1411,7 +1411,7 @@ hh_status hh_batch_create(hh_volume vol, const hh_camera* cams, int n_cams,
     b->bg = *bg;
     b->cams.assign(cams, cams + n_cams);
     b->outs.assign(outs, outs + n_cams);
-    b->cfg = hh_batch_config{128, 0, 32, 8, 0};
+    b->cfg = hh_batch_config{128, 0, 32, 8, 0, 0};
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -1504,7 +1504,10 @@ hh_status hh_batch_autotune(hh_batch b, int reps, void* stream, hh_batch_config*
         for (int tw : {8, 4, 16})
             for (int th : {128, 256, 64})
                 for (int rm : {32, 16, 8})
-                    for (int bps : {0, -2}) cand.push_back(hh_batch_config{th, bps, rm, tw, to});
+                    for (int bps : {0, -2})
+                        for (int tg : {0, 1})
+                            if (tg == 0 || rm == 32)
+                                cand.push_back(hh_batch_config{th, bps, rm, tw, to, tg});
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -117,7 +117,7 @@ struct hh_server_s {
     int device = 0;
     int sm_count = 0;
     int max_inflight = 1;
-    hh_batch_config cfg{128, 0, 32, 8, 0};
+    hh_batch_config cfg{128, 0, 32, 8, 0, 0};
     char* pool_base = nullptr;
     hh::OffsetPool pool;
     // the queue on the device
@@ -565,7 +565,8 @@ hh_status hh_serve_set_config(hh_server S, const hh_batch_config* cfg) {
     if (cfg->block_threads < 32 || cfg->block_threads > 256 || cfg->block_threads % 32 ||
         cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 64 || cfg->refill_min < 1 ||
         cfg->refill_min > 32 || (cfg->tile_w != 4 && cfg->tile_w != 8 && cfg->tile_w != 16) ||
-        (cfg->tile_order != 0 && cfg->tile_order != 1))
+        (cfg->tile_order != 0 && cfg->tile_order != 1) ||
+        (cfg->tile_group != 0 && cfg->tile_group != 1))
         return hh::fail(HH_ERR_INVALID_ARG, "invalid launch configuration");
     std::unique_lock<std::mutex> lock(S->mu);
     // the shape is the worker's: wait (bounded) until nothing is on the GPU

@@ -90,7 +90,7 @@ class hh_view_out(ctypes.Structure):
 class hh_batch_config(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("refill_min", ctypes.c_int), ("tile_w", ctypes.c_int),
-                ("tile_order", ctypes.c_int)]
+                ("tile_order", ctypes.c_int), ("tile_group", ctypes.c_int)]
 
 
 class hh_serve_stats(ctypes.Structure):
@@ -428,9 +428,9 @@ def hh_batch_create(vol: Volume, cams, params, bg, outs) -> Batch:
 
 
 def hh_batch_set_config(b: Batch, block_threads=128, blocks_per_sm=0, refill_min=32, tile_w=8,
-                        tile_order=0):
+                        tile_order=0, tile_group=0):
     c = hh_batch_config(int(block_threads), int(blocks_per_sm), int(refill_min), int(tile_w),
-                        int(tile_order))
+                        int(tile_order), int(tile_group))
     _check(load().hh_batch_set_config(b.handle, ctypes.byref(c)))
 
 
@@ -503,7 +503,7 @@ def hh_pipeline_create(grid: hh_grid, K_gd: float, max_particles: int, cams, par
     B = _background(bg)
     C = None if cfg is None else ctypes.byref(hh_batch_config(
         int(cfg["block_threads"]), int(cfg["blocks_per_sm"]), int(cfg["refill_min"]),
-        int(cfg["tile_w"]), int(cfg.get("tile_order", 0))))
+        int(cfg["tile_w"]), int(cfg.get("tile_order", 0)), int(cfg.get("tile_group", 0))))
     out = ctypes.c_void_p()
     _check(load().hh_pipeline_create(ctypes.byref(grid), float(K_gd), int(max_particles), c_cams,
                                      n, ctypes.byref(P), ctypes.byref(B), C, ctypes.byref(out)))
@@ -579,9 +579,9 @@ def hh_serve_create(mem_budget_bytes: int, max_slots: int) -> Server:
 
 
 def hh_serve_set_config(s: Server, block_threads=128, blocks_per_sm=0, refill_min=32, tile_w=8,
-                        tile_order=0):
+                        tile_order=0, tile_group=0):
     c = hh_batch_config(int(block_threads), int(blocks_per_sm), int(refill_min), int(tile_w),
-                        int(tile_order))
+                        int(tile_order), int(tile_group))
     _check(load().hh_serve_set_config(s.handle, ctypes.byref(c)))
 
 

@@ -51,7 +51,7 @@ def test_struct_layouts_match_header(lib):
                "hh_plane": ["origin", "u", "v", "rgb8_dev", "width", "height"],
                "hh_view_out": ["rgb", "exit_pos", "exit_dir", "steps", "flags", "rgb8"],
                "hh_batch_config": ["block_threads", "blocks_per_sm", "refill_min", "tile_w",
-                                   "tile_order"],
+                                   "tile_order", "tile_group"],
                "hh_serve_stats": ["submitted", "admitted", "completed", "cancelled", "failed",
                                   "rejected", "pending", "running", "rays_completed",
                                   "pool_used", "pool_capacity", "worker_launches",

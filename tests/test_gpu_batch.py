@@ -61,10 +61,14 @@ def scene(gpu):
     return dims, parts_t, bg, torch.from_numpy(bg).cuda()
 
 
-# (block_threads, blocks_per_sm, refill_min, tile_w, tile_order): tile-at-a-time and
-# warp refill, every tile shape, views one after the other and interleaved
-CONFIGS = [(128, 0, 32, 8, 0), (64, 0, 1, 8, 1), (256, 2, 8, 4, 0), (96, 1, 16, 16, 1),
-           (32, 3, 31, 8, 0), (128, 0, 32, 8, 1), (256, 0, 32, 4, 1)]
+# (block_threads, blocks_per_sm, refill_min, tile_w, tile_order, tile_group):
+# tile-at-a-time and warp refill, every tile shape, views one after the other and
+# interleaved, tiles taken by warps and by blocks (a block of 96 threads leaves a
+# group of 3 tiles that straddles view boundaries and the last, partial group)
+CONFIGS = [(128, 0, 32, 8, 0, 0), (64, 0, 1, 8, 1, 0), (256, 2, 8, 4, 0, 0),
+           (96, 1, 16, 16, 1, 0), (32, 3, 31, 8, 0, 0), (128, 0, 32, 8, 1, 0),
+           (256, 0, 32, 4, 1, 0), (256, 0, 32, 8, 0, 1), (96, 2, 32, 16, 1, 1),
+           (64, 0, 32, 4, 0, 1), (32, 0, 32, 8, 1, 1)]
 
 
 @pytest.mark.parametrize("storage,stepper,adaptive",
@@ -161,7 +165,8 @@ def test_batch_rejects_bad_configs(gpu, scene):
     outs = _outs(torch, cams)
     b = hh.hh_batch_create(vol, cams, f32(hi.params_rk4_fixed(dims)), bg_t, outs)
     for cfg in ((0, 0, 32, 8), (100, 0, 32, 8), (128, -1, 32, 8), (128, 0, 0, 8),
-                (128, 0, 33, 8), (128, 0, 32, 6), (128, 0, 32, 8, 2), (128, 0, 32, 8, -1)):
+                (128, 0, 33, 8), (128, 0, 32, 6), (128, 0, 32, 8, 2), (128, 0, 32, 8, -1),
+                (128, 0, 32, 8, 0, 2), (128, 0, 32, 8, 0, -1), (128, 0, 16, 8, 0, 1)):
         with pytest.raises(hh.HHError):
             hh.hh_batch_set_config(b, *cfg)
     with pytest.raises(hh.HHError):

@@ -93,19 +93,22 @@ def test_no_corner_index_leaves_the_padded_volume(debug_hh, oracle_lib, dims, st
         for params in _schedules(dims):
             params = f32(params)
             got = gpu_trace(hh, torch, vol, cams, params, bg_t)
-            # the same views through the persistent batched launch
-            outs = [{"rgb": torch.empty(c["width"] * c["height"] * 3, device="cuda")}
-                    for c in cams]
-            b = hh.hh_batch_create(vol, cams, params, bg_t, outs)
-            hh.hh_batch_set_config(b, 64, 0, 8, 4)
-            hh.hh_batch_launch(b)
-            torch.cuda.synchronize()
-            b.close()
-            assert hh.hh_debug_bounds_violations(reset=True) == 0, params
-            for c, g, o in zip(cams, got, outs):
+            # the same views through the persistent batched launch (warp refill,
+            # and tiles taken by blocks)
+            for cfg in ((64, 0, 8, 4), (96, 0, 32, 8, 1, 1)):
+                outs = [{"rgb": torch.empty(c["width"] * c["height"] * 3, device="cuda")}
+                        for c in cams]
+                b = hh.hh_batch_create(vol, cams, params, bg_t, outs)
+                hh.hh_batch_set_config(b, *cfg)
+                hh.hh_batch_launch(b)
+                torch.cuda.synchronize()
+                b.close()
+                assert hh.hh_debug_bounds_violations(reset=True) == 0, (params, cfg)
+                for g, o in zip(got, outs):
+                    assert np.array_equal(o["rgb"].cpu().numpy().reshape(-1, 3),
+                                          g["rgb"].astype(np.float32))
+            for c, g in zip(cams, got):
                 assert not np.any(g["flags"] & HH_FLAG_CLAMP)
-                assert np.array_equal(o["rgb"].cpu().numpy().reshape(-1, 3),
-                                      g["rgb"].astype(np.float32))
                 ref = oracle_lib.trace_grid(vol4, c, params, bg, nthreads=4)
                 assert_parity_conditioned(g, ref, oracle_lib, field, dims, c, params)
         vol.close()

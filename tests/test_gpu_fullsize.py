@@ -172,7 +172,7 @@ def test_fullsize_8view_fp16_batched_launch_equals_trace(gpu, scene):
     ref = gpu_trace(hh, torch, vol, cams, params, bg_t, want_all=False)
     outs = [{"rgb": torch.empty(c["width"] * c["height"] * 3, device="cuda")} for c in cams]
     b = hh.hh_batch_create(vol, cams, params, bg_t, outs)
-    hh.hh_batch_set_config(b, 256, 0, 32, 4)  # the configuration the autotuner keeps here
+    hh.hh_batch_set_config(b, 256, 0, 32, 4, 1, 0)  # the configuration the autotuner keeps here
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         for _ in range(2):
@@ -207,7 +207,7 @@ def test_fullsize_512_fp16_32_views_batched(gpu, oracle_lib):
                      "steps": torch.empty(n, dtype=torch.int32, device="cuda"),
                      "flags": torch.empty(n, dtype=torch.int32, device="cuda")})
     b = hh.hh_batch_create(vol, cams, params, bg_t, outs)
-    hh.hh_batch_set_config(b, 128, 0, 32, 8)  # the configuration the autotuner keeps here
+    hh.hh_batch_set_config(b, 128, 0, 32, 4, 1, 1)  # the configuration the autotuner keeps here
     hh.hh_batch_launch(b)
     torch.cuda.synchronize()
     got = [{k: (v.cpu().numpy().reshape(-1, 3).astype(np.float64) if k in ("rgb", "exit_pos",
