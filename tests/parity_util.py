@@ -177,39 +177,39 @@ def perturbation_spread(oracle, field, box, C0, w0, params, n_pert=6, seed=0, nt
     return s_dir, s_pos, s_steps
 
 
-def path_spread(oracle, field, box, C0, w0, params, n_pert=3, seed=2, nthreads=8):
+def path_spread(oracle, field, box, C0, w0, params, nthreads=8):
     """Accumulated sensitivity to rounding at every step. An FP32 march rounds
     at each of its K steps, not only at the start: its sample position is the
-    position rounded to FP32 (up to half an ulp of the box extent, 2^-24 of
-    it), while the direction (carried as a small deflection of the primary
-    direction) and the compensated position carry far smaller errors. The
-    oracle's march depends only on the current state (C_k, w_k), so restarting
-    it from each recorded state with the position moved by that half ulp gives
-    the sensitivity s_k of the exit to the rounding of step k; independent
-    errors add as sqrt(sum_k s_k^2). Returns that for the exit direction and
-    position, and whether some restart changed the step count."""
-    r = np.random.default_rng(seed)
+    position rounded to FP32, each coordinate on its own by up to half an ulp
+    of the box extent (2^-24 of it), while the direction (carried as a small
+    deflection of the primary direction) and the compensated position carry
+    far smaller errors. The oracle's march depends only on the current state
+    (C_k, w_k), so restarting it from each recorded state with the position
+    moved by that half ulp along x, along y and along z gives the exit's
+    response to each coordinate's rounding at step k; their sum s_k is the
+    first-order change for the worst signs of the three roundings, and
+    independent steps add as sqrt(sum_k s_k^2). Returns that for the exit
+    direction and position, and whether some restart changed the step count."""
     pos_eps = 2.0**-24 * float(max(box))
     out_dir = np.zeros(len(C0))
     out_pos = np.zeros(len(C0))
     out_steps = np.zeros(len(C0), dtype=bool)
+    axes = pos_eps * np.eye(3)
     for i in range(len(C0)):
         m = oracle.march_ray(field, box, C0[i], w0[i], params, path_cap=int(params["max_steps"]))
         path = m["path"]
         K = len(path)
         if K == 0:
             continue
-        Ck = np.repeat(path[:, 0:3], n_pert, axis=0)
-        wk = np.repeat(path[:, 3:6], n_pert, axis=0)
-        dc = r.normal(size=Ck.shape)
-        dc *= pos_eps / np.linalg.norm(dc, axis=1, keepdims=True)
-        q = oracle.march_rays(field, box, Ck + dc, wk, params, nthreads=nthreads)
-        sd = angle(q["exit_dir"], m["exit_dir"]).reshape(K, n_pert).max(axis=1)
-        sp = np.abs(q["exit_pos"] - m["exit_pos"]).max(axis=1).reshape(K, n_pert).max(axis=1)
+        Ck = (path[:, None, 0:3] + axes[None]).reshape(-1, 3)
+        wk = np.repeat(path[:, 3:6], 3, axis=0)
+        q = oracle.march_rays(field, box, Ck, wk, params, nthreads=nthreads)
+        sd = angle(q["exit_dir"], m["exit_dir"]).reshape(K, 3).sum(axis=1)
+        sp = np.abs(q["exit_pos"] - m["exit_pos"]).max(axis=1).reshape(K, 3).sum(axis=1)
         remaining = m["steps"] - np.arange(K)
         out_dir[i] = np.sqrt(np.sum(sd**2))
         out_pos[i] = np.sqrt(np.sum(sp**2))
-        out_steps[i] = bool(np.any(q["steps"].reshape(K, n_pert) != remaining[:, None]))
+        out_steps[i] = bool(np.any(q["steps"].reshape(K, 3) != remaining[:, None]))
     return out_dir, out_pos, out_steps
 
 
@@ -322,6 +322,10 @@ def assert_parity_conditioned(gpu: dict, ref: dict, oracle, field, box, cam, par
             s_pos[j] = np.maximum(s_pos[j], p_pos)
             over = over_of()
             st["n_path"] = int(len(j))
+            # how close the rays measured along their path come to that bound
+            st["worst_path_over_bound"] = float(max(
+                (ang[idx][j] / (DIR_TOL + 5 * s_dir[j] + turn[j])).max(),
+                (pos[idx][j] / (POS_TOL + 5 * s_pos[j])).max()))
         excess = ang[idx] / (DIR_TOL + 5 * s_dir + turn)
         st["worst_over_bound"] = float(excess.max())
         if over.any():
