@@ -229,9 +229,11 @@ hh_status hh_build_index_field_noalloc(const hh_particles* particles, const hh_g
  * into dst_dev: nx*ny*nz*4 floats {dn, gx, gy, gz} per voxel (x fastest). */
 hh_status hh_volume_export(hh_volume vol, float* dst_dev, void* stream);
 
-/* Grid, FP16 scales (1 for FP32 storage) and device bytes of a volume
- * (bookkeeping; no paper passage). Synchronises `stream` to read the scales.
- * Any output may be NULL. */
+/* Grid, FP16 scales (1 for FP32 storage) and device bytes of a volume's
+ * packed field (bookkeeping; no paper passage; the same allocation also holds
+ * a free-cell mask, one bit per 4^3 voxels, and its build scratch, a byte per
+ * stored column and 16 slices: under 1 % more). Synchronises `stream` to read
+ * the scales. Any output may be NULL. */
 hh_status hh_volume_info(hh_volume vol, hh_grid* grid, float* s_n, float* s_g, size_t* bytes,
                          void* stream);
 

@@ -17,6 +17,12 @@
 // 32-byte sectors. The volume stores are marked evict-first (st.global.cs):
 // the volume outgrows L2 anyway, and this keeps the density, which the
 // kernel is still reading, resident in L2 instead.
+// BRICK2 builds also leave the volume's free-cell mask (the march skips the
+// eight loads of a sample whose corners are all zero): the store pass records
+// per column and run which 4-slice cells hold a nonzero stored voxel (a
+// byte, no atomics), and free_mask_kernel turns those bytes into one bit per
+// 4^3 cell. The store passes walk their runs unrolled by 2, not 4: with the
+// column's bits to carry, 4 spilled and was slower.
 #include "hh_internal.h"
 
 namespace hh {
@@ -29,6 +35,10 @@ struct Cell {
 struct OutLayout {
     int layout;
     unsigned bx, bxy;
+    uint8_t* colbits;     // BRICK2: per stored (padded) column and z run, the z cells
+                          // where it stored a nonzero voxel (null: none); rows of
+                          // `pitch` bytes
+    int pitch;
 };
 
 // Element of grid voxel (i, j, k) in the output layout (BRICK2: halo offset).
@@ -57,7 +67,8 @@ __device__ __forceinline__ float scale_of(unsigned bits) {
 #define FIELD_ZRUN 16
 
 // 8 resident blocks of 256 threads for every mode (32 registers); the FP16
-// store pass with 5 (48 registers) was 6-8 % slower.
+// store pass with 5 (48 registers) was 6-8 % slower, and with 6 or 7 it
+// spilled more, not less.
 template <int MODE>  // 0: FP32 store, 1: FP16 max pass, 2: FP16 store
 __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __restrict__ rho, int nx,
                                                            int ny, int nz, float K, OutLayout L,
@@ -87,6 +98,11 @@ __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __res
         scales[1] = s_g;
     }
     float mn = 0.0f, mg = 0.0f;
+    // occupancy (the store passes): bit k - k0 set when this column stored a
+    // nonzero voxel at grid slice k (padded k + 1; the halo slices repeat
+    // slices 0 and nz - 1)
+    constexpr bool OCC = MODE != 1;
+    unsigned nzk = 0;
     if (J < Hh) {
         const int i = min(max(I - h, 0), nx - 1), j = min(max(J - h, 0), ny - 1);
         const size_t sy = nx, sz = static_cast<size_t>(nx) * ny;
@@ -94,7 +110,7 @@ __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __res
         const bool xl = i > 0, xh = i < nx - 1, yl = j > 0, yh = j < ny - 1;
         float dprev = k0 > 0 ? K * __ldg(col + (k0 - 1) * sz) : 0.0f;
         float dcur = K * __ldg(col + k0 * sz);
-#pragma unroll 4
+#pragma unroll(MODE == 1 ? 4 : 2)
         for (int k = k0; k < k1; ++k) {
             const float* c = col + k * sz;
             const float dnext = (k + 1 < nz) ? K * __ldg(c + sz) : 0.0f;
@@ -110,10 +126,12 @@ __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __res
             // z halo copies of the first and last slice
             const bool zh = h && (k == 0 || k == nz - 1);
             const size_t oh = zh ? brick2_offset(I, J, k == 0 ? 0 : nz + 1, L.bx, L.bxy) : 0;
+            bool nonzero = false;
             if (MODE == 0) {
                 const float4 v = make_float4(e.dn, e.gx, e.gy, e.gz);
                 __stcs(static_cast<float4*>(out) + o, v);
                 if (zh) __stcs(static_cast<float4*>(out) + oh, v);
+                nonzero = v.x != 0.0f || v.y != 0.0f || v.z != 0.0f || v.w != 0.0f;
             } else if (MODE == 1) {
                 mn = fmaxf(mn, fabsf(e.dn));
                 mg = fmaxf(mg, fmaxf(fabsf(e.gx), fmaxf(fabsf(e.gy), fabsf(e.gz))));
@@ -127,10 +145,29 @@ __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __res
                                            static_cast<unsigned>(q.z) | (static_cast<unsigned>(q.w) << 16));
                 __stcs(static_cast<uint2*>(out) + o, w);
                 if (zh) __stcs(static_cast<uint2*>(out) + oh, w);
+                nonzero = ((w.x | w.y) & 0x7FFF7FFFu) != 0u;  // a half other than +-0
             }
+            if (OCC) nzk |= static_cast<unsigned>(nonzero) << (k - k0);  // k - k0 < 16
             dprev = dcur;
             dcur = dnext;
         }
+    }
+    if (OCC && L.colbits && J < Hh) {
+        // the padded z cells (k + 1) >> 2 of the slices marked (the halo slice
+        // 0 shares slice 0's cell; nz + 1 may open the next), bit b for cell
+        // (k0 >> 2) + b (b <= 4): one byte per stored column and run, no
+        // atomics
+        // k0 is a multiple of 16, so slice k0 + t (padded k0 + t + 1) lies in
+        // cell offset (t + 1) >> 2: t 0-2 -> 0, 3-6 -> 1, 7-10 -> 2, 11-14 -> 3,
+        // 15 -> 4; the halo slice nz + 1 repeats slice nz - 1 = k0 + t' at
+        // cell offset (t' + 2) >> 2
+        static_assert(FIELD_ZRUN == 16, "cell offsets assume 16-slice runs");
+        unsigned zbits = ((nzk & 0x0007u) ? 1u : 0u) | ((nzk & 0x0078u) ? 2u : 0u) |
+                         ((nzk & 0x0780u) ? 4u : 0u) | ((nzk & 0x7800u) ? 8u : 0u) |
+                         ((nzk & 0x8000u) ? 16u : 0u);
+        if (k1 == nz && ((nzk >> (nz - 1 - k0)) & 1u)) zbits |= 1u << ((nz + 1 - k0) >> 2);
+        L.colbits[(static_cast<size_t>(blockIdx.y) * Hh + J) * L.pitch + I] =
+            static_cast<uint8_t>(zbits);
     }
     if (MODE == 1) {  // block maximum, then one atomic per block
         for (int o = 16; o > 0; o >>= 1) {
@@ -152,6 +189,48 @@ __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __res
             atomicMax(max_bits + 1, __float_as_uint(mg));
         }
     }
+}
+
+// The free-cell mask from the store pass's column bytes. Cell c = (cx, cy,
+// cz) of padded indices is free when none of the cells c + {0,1}^3 (the eight
+// corners of any sample whose first corner lies in c are in them) holds a
+// stored nonzero voxel: no column of x in 4cx .. 4cx + 7, y in 4cy .. 4cy + 7
+// marked z cell cz or cz + 1 in a run whose byte covers it (run r covers
+// cells 4r .. 4r + 7, bit cz - 4r). The four bytes of four columns are one
+// aligned 32-bit word (rows are padded to 4 bytes, the padding never
+// written, so zero). One thread per cell, x fastest; a warp writes one word.
+__global__ void free_mask_kernel(const uint8_t* __restrict__ colbits, int pitch, int H, int runs,
+                                 unsigned ncx, unsigned ncy, unsigned ncz,
+                                 unsigned* __restrict__ fr, unsigned words) {
+    const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned ncxy = ncx * ncy;
+    bool any = true;
+    if (c < ncxy * ncz) {
+        any = false;
+        const unsigned cz = c / ncxy, rem = c - cz * ncxy, cy = rem / ncx, cx = rem - cy * ncx;
+        const bool two_words = 4 * cx + 4 < static_cast<unsigned>(pitch);
+        const int j1 = min(4 * static_cast<int>(cy) + 8, H);
+        // runs whose bytes cover cell cz or cz + 1
+        const int r0 = static_cast<int>(cz) >= 7 ? (static_cast<int>(cz) - 4) >> 2 : 0;
+        const int r1 = min((static_cast<int>(cz) + 1) >> 2, runs - 1);
+        for (int r = r0; r <= r1; ++r) {
+            unsigned sel = 0;
+            for (int d = 0; d < 2; ++d) {
+                const int b = static_cast<int>(cz) + d - 4 * r;
+                if (b >= 0 && b <= 7 && cz + d < ncz) sel |= 0x01010101u << b;
+            }
+            if (!sel) continue;
+            for (int J = 4 * static_cast<int>(cy); J < j1; ++J) {
+                const unsigned* row = reinterpret_cast<const unsigned*>(
+                    colbits + (static_cast<size_t>(r) * H + J) * pitch + 4 * cx);
+                unsigned v = __ldg(row);
+                if (two_words) v |= __ldg(row + 1);
+                any |= (v & sel) != 0u;
+            }
+        }
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, !any);
+    if ((threadIdx.x & 31) == 0 && (c >> 5) < words) fr[c >> 5] = word;
 }
 
 __global__ void export_kernel(const void* __restrict__ data, int storage, OutLayout L, int nx,
@@ -187,27 +266,39 @@ cudaError_t launch_field(const float* rho, int nx, int ny, int nz, float K, hh_v
                     (nz + FIELD_ZRUN - 1) / FIELD_ZRUN);
     const dim3 grid_max(static_cast<unsigned>((static_cast<int64_t>(nx) * ny + 255) / 256),
                         (nz + FIELD_ZRUN - 1) / FIELD_ZRUN);
-    const OutLayout L{vol->layout, vol->bx, vol->bxy};
+    const bool masks = vol->layout == HH_LAYOUT_BRICK2 && vol->colbits_dev != nullptr;
+    const int pitch = (nx + 2 + 3) & ~3;
+    const int runs = (nz + FIELD_ZRUN - 1) / FIELD_ZRUN;
+    const OutLayout L{vol->layout, vol->bx, vol->bxy, masks ? vol->colbits_dev : nullptr, pitch};
+    cudaError_t e = cudaSuccess;
     if (vol->storage == HH_STORE_FP32) {
         field_column_kernel<0><<<grid, block, 0, s>>>(rho, nx, ny, nz, K, L, vol->data, nullptr,
                                                       vol->scales_dev);
         count_launch();
-        return cudaGetLastError();
+    } else {
+        e = cudaMemsetAsync(vol->max_dev, 0, 2 * sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        field_column_kernel<1><<<grid_max, block, 0, s>>>(rho, nx, ny, nz, K, L, nullptr,
+                                                          vol->max_dev, vol->scales_dev);
+        field_column_kernel<2><<<grid, block, 0, s>>>(rho, nx, ny, nz, K, L, vol->data,
+                                                      vol->max_dev, vol->scales_dev);
+        count_launch(2);
     }
-    cudaError_t e = cudaMemsetAsync(vol->max_dev, 0, 2 * sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    field_column_kernel<1><<<grid_max, block, 0, s>>>(rho, nx, ny, nz, K, L, nullptr, vol->max_dev,
-                                                  vol->scales_dev);
-    field_column_kernel<2><<<grid, block, 0, s>>>(rho, nx, ny, nz, K, L, vol->data, vol->max_dev,
-                                                  vol->scales_dev);
-    count_launch(2);
+    if (masks) {
+        const size_t cells = static_cast<size_t>(vol->ncx) * vol->ncy * vol->ncz;
+        const unsigned blocks = static_cast<unsigned>((cells + 255) / 256);
+        free_mask_kernel<<<blocks, 256, 0, s>>>(vol->colbits_dev, pitch, ny + 2, runs, vol->ncx,
+                                                vol->ncy, vol->ncz, vol->free_dev,
+                                                static_cast<unsigned>(vol->mask_words));
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_export(const hh_volume_s* vol, float4* dst, cudaStream_t s) {
     const dim3 block(32, 8);
     const dim3 grid((vol->nx + 31) / 32, (vol->ny + 7) / 8, vol->nz);
-    const OutLayout L{vol->layout, vol->bx, vol->bxy};
+    const OutLayout L{vol->layout, vol->bx, vol->bxy, nullptr, 0};
     export_kernel<<<grid, block, 0, s>>>(vol->data, vol->storage, L, vol->nx, vol->ny, vol->nz,
                                          vol->scales_dev, dst);
     count_launch();

@@ -1,0 +1,89 @@
+"""The march's free-cell skip on fields built to catch a wrong skip.
+
+A volume's free-cell mask marks the 4^3 cells of padded lattice indices
+whose samples read eight zero corners; the march takes such a sample as zero
+without reading the bricks. Here the field is zero except at single voxels
+with strong values, placed on the edges of the cells (padded indices 3, 4, 7,
+8), at the grid's faces (whose halo copies sit in the first and last cells)
+and in the last, partial cells of ragged grids. A nonzero sample taken for
+zero would turn a passing ray by about 1e-3 rad, a thousand times the
+tolerance, so every ray is held to the oracle with no excusal (fixed steps,
+where the march is well conditioned), from several sides, on FP32 and FP16
+volumes, through hh_trace and the batched launch.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import hh_inputs as hi
+from parity_util import assert_parity_plain, export_volume, f32, gpu_trace
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2603_02048_gb300 import hh
+
+    return hh, torch
+
+
+def _spikes(dims, seed):
+    """Zero dn with single voxels on cell edges, at the faces and in the
+    last cells: grid index g has padded index g + 1, cells of 4 padded
+    indices."""
+    nx, ny, nz = dims
+    dn = np.zeros((nz, ny, nx))
+
+    def picks(n):
+        # grid indices whose padded index g + 1 is 3, 4, 7 or 8, plus the faces
+        return sorted({g for g in (0, 2, 3, 6, 7, n - 2, n - 1) if 0 <= g < n})
+
+    rng = np.random.default_rng(seed)
+    for x, y, z in itertools.product(picks(nx), picks(ny), picks(nz)):
+        if rng.random() < 0.35:
+            dn[z, y, x] = rng.choice([-1.0, 1.0]) * rng.uniform(1e-3, 3e-3)
+    return dn
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("dims", [(16, 16, 16), (13, 10, 17), (9, 22, 6)])
+def test_isolated_voxels_on_cell_edges(gpu, oracle_lib, dims, storage):
+    hh, torch = gpu
+    dn = _spikes(dims, seed=sum(dims))
+    bg = hi.checker_background()
+    bg_t = torch.from_numpy(bg).cuda()
+    vol = hh.hh_volume_from_dn(torch.from_numpy(dn.astype(np.float32).ravel()).cuda(),
+                               hh.make_grid(dims, 2.0, storage))
+    vol4 = export_volume(hh, torch, vol, dims)
+    assert np.count_nonzero(vol4[..., 0]) > 4  # the spikes are there
+    cams = f32([hi.orbit_camera(dims, az, el, 48, 40, dist_factor=1.2)
+                for az, el in ((0.0, 0.0), (90.0, 25.0), (200.0, -40.0), (315.0, 60.0))])
+    params = f32(hi.params_euler_adaptive(dims))
+    params.update(adaptive=False, h_fixed=0.5, h_min=0.5, h_max=0.5,
+                  max_steps=hi.default_max_steps(dims, 0.5))
+    got = gpu_trace(hh, torch, vol, cams, params, bg_t)
+    # the same views through the batched launch, bit for bit
+    outs = [{"rgb": torch.empty(c["width"] * c["height"] * 3, device="cuda")} for c in cams]
+    b = hh.hh_batch_create(vol, cams, params, bg_t, outs)
+    hh.hh_batch_set_config(b, 64, 0, 32, 8, 1, 1)
+    hh.hh_batch_launch(b)
+    torch.cuda.synchronize()
+    b.close()
+    hits = 0
+    for c, g, o in zip(cams, got, outs):
+        assert np.array_equal(o["rgb"].cpu().numpy().reshape(-1, 3), g["rgb"].astype(np.float32))
+        ref = oracle_lib.trace_grid(vol4, c, params, bg, nthreads=4)
+        st = assert_parity_plain(g, ref, dims)
+        hits += st["hits"]
+        # rays that pass a spike are turned: the field is not skipped wholesale
+        assert np.any(g["flags"] & 1)
+    assert hits > 1000
+    vol.close()
