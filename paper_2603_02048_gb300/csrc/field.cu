@@ -153,14 +153,12 @@ __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __res
         }
     }
     if (OCC && L.colbits && J < Hh) {
-        // the padded z cells (k + 1) >> 2 of the slices marked (the halo slice
-        // 0 shares slice 0's cell; nz + 1 may open the next), bit b for cell
-        // (k0 >> 2) + b (b <= 4): one byte per stored column and run, no
-        // atomics
-        // k0 is a multiple of 16, so slice k0 + t (padded k0 + t + 1) lies in
-        // cell offset (t + 1) >> 2: t 0-2 -> 0, 3-6 -> 1, 7-10 -> 2, 11-14 -> 3,
-        // 15 -> 4; the halo slice nz + 1 repeats slice nz - 1 = k0 + t' at
-        // cell offset (t' + 2) >> 2
+        // one byte per stored column and run (no atomics), bit b for padded z
+        // cell (k0 >> 2) + b: k0 is a multiple of 16, so slice k0 + t (padded
+        // k0 + t + 1) lies in cell offset (t + 1) >> 2 (t 0-2 -> 0, 3-6 -> 1,
+        // 7-10 -> 2, 11-14 -> 3, 15 -> 4); the halo slice 0 shares slice 0's
+        // cell, and the halo slice nz + 1, a copy of slice nz - 1 = k0 + t',
+        // lies in cell offset (t' + 2) >> 2
         static_assert(FIELD_ZRUN == 16, "cell offsets assume 16-slice runs");
         unsigned zbits = ((nzk & 0x0007u) ? 1u : 0u) | ((nzk & 0x0078u) ? 2u : 0u) |
                          ((nzk & 0x0780u) ? 4u : 0u) | ((nzk & 0x7800u) ? 8u : 0u) |
