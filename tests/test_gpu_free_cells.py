@@ -87,3 +87,36 @@ def test_isolated_voxels_on_cell_edges(gpu, oracle_lib, dims, storage):
         assert np.any(g["flags"] & 1)
     assert hits > 1000
     vol.close()
+
+
+def test_rebuild_refreshes_the_free_cells(gpu, oracle_lib):
+    """A volume built from a blob in one corner, marched, then rebuilt from a
+    blob reaching into the cells that were free: the march of the rebuilt
+    volume must see the new blob (a mask left from the first build would skip
+    it and turn the rays that cross it by far more than the tolerance)."""
+    hh, torch = gpu
+    dims = (48, 48, 48)
+    K = float(np.float32(hi.K_GD))
+    pa = hi.plume_particles(6000, 24, seed=31)
+    pa[:, :3] += 4.0
+    pb = hi.plume_particles(6000, 24, seed=32)
+    pb[:, :3] += 20.0
+    bg = hi.checker_background()
+    bg_t = torch.from_numpy(bg).cuda()
+    cams = f32([hi.orbit_camera(dims, 20.0, 15.0, 64, 48, dist_factor=1.2)])
+    params = f32(hi.params_euler_adaptive(dims))
+    params.update(adaptive=False, h_fixed=0.5, h_min=0.5, h_max=0.5,
+                  max_steps=hi.default_max_steps(dims, 0.5))
+    vol = hh.hh_build_index_field(torch.from_numpy(pa).cuda(), hh.make_grid(dims, 2.0), K)
+    first = gpu_trace(hh, torch, vol, cams, params, bg_t)
+    hh.hh_volume_rebuild(vol, torch.from_numpy(pb).cuda(), K)
+    got = gpu_trace(hh, torch, vol, cams, params, bg_t)
+    vol4 = export_volume(hh, torch, vol, dims)
+    # the far corner, empty in the first build, holds the second blob
+    assert np.abs(vol4[36:44, 36:44, 36:44, 0]).max() > 0.0
+    ref = oracle_lib.trace_grid(vol4, cams[0], params, bg, nthreads=4)
+    st = assert_parity_plain(got[0], ref, dims)
+    assert st["hits"] > 1000
+    # and the two builds march differently
+    assert not np.array_equal(first[0]["exit_dir"], got[0]["exit_dir"])
+    vol.close()
