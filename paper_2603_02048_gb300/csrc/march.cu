@@ -28,6 +28,10 @@
 // 2x2x2 micro-bricks (BRICK2) with a one-voxel halo of edge copies: the
 // bricks spread the distinct voxels of a warp's corner load over all L1 bank
 // groups, and the halo lets a sample in the box skip every index clamp.
+// A sample whose eight corners are all zero (its first corner in a free cell
+// of the volume's mask, built with the volume) is read as zero from one bit
+// of that mask instead of eight brick loads; every step is still taken, so
+// the results are the same bit for bit.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
