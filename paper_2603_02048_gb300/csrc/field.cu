@@ -17,12 +17,12 @@
 // 32-byte sectors. The volume stores are marked evict-first (st.global.cs):
 // the volume outgrows L2 anyway, and this keeps the density, which the
 // kernel is still reading, resident in L2 instead.
-// BRICK2 builds also leave the volume's free-cell mask (the march skips the
+// BRICK2 builds also leave the volume's free-brick mask (the march skips the
 // eight loads of a sample whose corners are all zero): the store pass records
-// per column and run which 4-slice cells hold a nonzero stored voxel (a
-// byte, no atomics), and free_mask_kernel turns those bytes into one bit per
-// 4^3 cell. The store passes walk their runs unrolled by 2, not 4: with the
-// column's bits to carry, 4 spilled and was slower.
+// per column and run which z bricks (pairs of padded slices) hold a nonzero
+// stored voxel (16 bits, no atomics), and free_mask_kernel turns those into
+// one bit per brick. The store passes walk their runs unrolled by 2, not 4:
+// with the column's bits to carry, 4 spilled and was slower.
 #include "hh_internal.h"
 
 namespace hh {
@@ -35,9 +35,9 @@ struct Cell {
 struct OutLayout {
     int layout;
     unsigned bx, bxy;
-    uint8_t* colbits;     // BRICK2: per stored (padded) column and z run, the z cells
+    uint16_t* colbits;    // BRICK2: per stored (padded) column and z run, the z bricks
                           // where it stored a nonzero voxel (null: none); rows of
-                          // `pitch` bytes
+                          // `pitch` columns
     int pitch;
 };
 
@@ -153,19 +153,23 @@ __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __res
         }
     }
     if (OCC && L.colbits && J < Hh) {
-        // one byte per stored column and run (no atomics), bit b for padded z
-        // cell (k0 >> 2) + b: k0 is a multiple of 16, so slice k0 + t (padded
-        // k0 + t + 1) lies in cell offset (t + 1) >> 2 (t 0-2 -> 0, 3-6 -> 1,
-        // 7-10 -> 2, 11-14 -> 3, 15 -> 4); the halo slice 0 shares slice 0's
-        // cell, and the halo slice nz + 1, a copy of slice nz - 1 = k0 + t',
-        // lies in cell offset (t' + 2) >> 2
-        static_assert(FIELD_ZRUN == 16, "cell offsets assume 16-slice runs");
-        unsigned zbits = ((nzk & 0x0007u) ? 1u : 0u) | ((nzk & 0x0078u) ? 2u : 0u) |
-                         ((nzk & 0x0780u) ? 4u : 0u) | ((nzk & 0x7800u) ? 8u : 0u) |
-                         ((nzk & 0x8000u) ? 16u : 0u);
-        if (k1 == nz && ((nzk >> (nz - 1 - k0)) & 1u)) zbits |= 1u << ((nz + 1 - k0) >> 2);
+        // 16 bits per stored column and run (no atomics), bit m for padded z
+        // brick (k0 >> 1) + m: k0 is a multiple of 16, so slice k0 + t (padded
+        // k0 + t + 1) lies in brick offset (t + 1) >> 1 (t = 0 -> 0, 1-2 -> 1,
+        // ..., 13-14 -> 7, 15 -> 8): bit 0 is slice bit 0 and bit m >= 1 the
+        // OR of slice bits 2m - 1 and 2m, i.e. the odd bits of
+        // nzk | (nzk >> 1), gathered. The halo slice 0 shares slice 0's
+        // brick, and the halo slice nz + 1, a copy of slice nz - 1 = k0 + t',
+        // lies in brick offset (t' + 2) >> 1.
+        static_assert(FIELD_ZRUN == 16, "brick offsets assume 16-slice runs");
+        unsigned odd = ((nzk | (nzk >> 1)) >> 1) & 0x5555u;  // bit 2i: slices 2i + 1, 2i + 2
+        odd = (odd | (odd >> 1)) & 0x3333u;
+        odd = (odd | (odd >> 2)) & 0x0F0Fu;
+        odd = (odd | (odd >> 4)) & 0x00FFu;                   // bit i: brick offset i + 1
+        unsigned zbits = (odd << 1) | (nzk & 1u);
+        if (k1 == nz && ((nzk >> (nz - 1 - k0)) & 1u)) zbits |= 1u << ((nz + 1 - k0) >> 1);
         L.colbits[(static_cast<size_t>(blockIdx.y) * Hh + J) * L.pitch + I] =
-            static_cast<uint8_t>(zbits);
+            static_cast<uint16_t>(zbits);
     }
     if (MODE == 1) {  // block maximum, then one atomic per block
         for (int o = 16; o > 0; o >>= 1) {
@@ -189,46 +193,59 @@ __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __res
     }
 }
 
-// The free-cell mask from the store pass's column bytes. Cell c = (cx, cy,
-// cz) of padded indices is free when none of the cells c + {0,1}^3 (the eight
-// corners of any sample whose first corner lies in c are in them) holds a
-// stored nonzero voxel: no column of x in 4cx .. 4cx + 7, y in 4cy .. 4cy + 7
-// marked z cell cz or cz + 1 in a run whose byte covers it (run r covers
-// cells 4r .. 4r + 7, bit cz - 4r). The four bytes of four columns are one
-// aligned 32-bit word (rows are padded to 4 bytes, the padding never
-// written, so zero). One thread per cell, x fastest; a warp writes one word.
-__global__ void free_mask_kernel(const uint8_t* __restrict__ colbits, int pitch, int H, int runs,
-                                 unsigned ncx, unsigned ncy, unsigned ncz,
-                                 unsigned* __restrict__ fr, unsigned words) {
-    const unsigned c = blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned ncxy = ncx * ncy;
-    bool any = true;
-    if (c < ncxy * ncz) {
-        any = false;
-        const unsigned cz = c / ncxy, rem = c - cz * ncxy, cy = rem / ncx, cx = rem - cy * ncx;
-        const bool two_words = 4 * cx + 4 < static_cast<unsigned>(pitch);
-        const int j1 = min(4 * static_cast<int>(cy) + 8, H);
-        // runs whose bytes cover cell cz or cz + 1
-        const int r0 = static_cast<int>(cz) >= 7 ? (static_cast<int>(cz) - 4) >> 2 : 0;
-        const int r1 = min((static_cast<int>(cz) + 1) >> 2, runs - 1);
-        for (int r = r0; r <= r1; ++r) {
-            unsigned sel = 0;
-            for (int d = 0; d < 2; ++d) {
-                const int b = static_cast<int>(cz) + d - 4 * r;
-                if (b >= 0 && b <= 7 && cz + d < ncz) sel |= 0x01010101u << b;
-            }
-            if (!sel) continue;
-            for (int J = 4 * static_cast<int>(cy); J < j1; ++J) {
+// The free-brick mask from the store pass's column bits. Brick B = (bx, by,
+// bz) of padded indices is free when none of the bricks B + {0,1}^3 (the
+// eight corners of any sample whose first corner lies in B are in them)
+// holds a stored nonzero voxel. A thread takes the 4x4 columns x in
+// 2bx .. 2bx + 3, y in 2by .. 2by + 3 (the 16-bit entries of two columns 2c,
+// 2c + 1 are one aligned 32-bit word; rows are padded to 4 columns, the
+// padding never written, so zero) and runs r and r + 1: run r's bits cover
+// z bricks 8r .. 8r + 8 and run r + 1's 8r + 8 .. 8r + 16, so their OR
+// gives the occupancy of z bricks 8r + 1 .. 8r + 9 in full (and of brick 0
+// for r = 0), hence the bits of bricks bz = 8r + 1 .. 8r + 8 (and 0). A warp
+// is 32 consecutive bx: for each bz its 32 bits are consecutive in the mask
+// (bricks in their own order, x fastest) and are ORed into the two words
+// they straddle; the mask is cleared before.
+__global__ void free_mask_kernel(const uint16_t* __restrict__ colbits, int pitch, int H, int runs,
+                                 unsigned nbx, unsigned nby, unsigned nbz,
+                                 unsigned* __restrict__ fr) {
+    const unsigned bx = blockIdx.x * 32 + threadIdx.x;
+    const unsigned by = blockIdx.y * blockDim.y + threadIdx.y;
+    const int r = static_cast<int>(blockIdx.z);
+    if (by >= nby) return;  // whole warps: threadIdx.y is one warp's
+    unsigned occ = 0;       // bit m: z brick 8r + m holds a nonzero voxel (m = 0 .. 16)
+    if (bx < nbx) {
+        const bool two_words = 2 * bx + 2 < static_cast<unsigned>(pitch);
+        const int j1 = min(2 * static_cast<int>(by) + 4, H);
+        for (int q = 0; q < 2 && r + q < runs; ++q) {
+            unsigned v = 0;
+            for (int J = 2 * static_cast<int>(by); J < j1; ++J) {
                 const unsigned* row = reinterpret_cast<const unsigned*>(
-                    colbits + (static_cast<size_t>(r) * H + J) * pitch + 4 * cx);
-                unsigned v = __ldg(row);
+                    colbits + (static_cast<size_t>(r + q) * H + J) * pitch + 2 * bx);
+                v |= __ldg(row);
                 if (two_words) v |= __ldg(row + 1);
-                any |= (v & sel) != 0u;
             }
+            occ |= ((v | (v >> 16)) & 0x1FFu) << (8 * q);
         }
     }
-    const unsigned word = __ballot_sync(0xffffffffu, !any);
-    if ((threadIdx.x & 31) == 0 && (c >> 5) < words) fr[c >> 5] = word;
+    const unsigned busy = occ | (occ >> 1);  // bit m: brick 8r + m or 8r + m + 1 occupied
+    const unsigned lane = threadIdx.x;
+    const unsigned row0 = by * nbx + blockIdx.x * 32;  // mask bit of lane 0, less bz * nbxy
+    const unsigned nbxy = nbx * nby;
+    for (int m = (r == 0) ? 0 : 1; m <= 8; ++m) {
+        const unsigned bz = 8u * static_cast<unsigned>(r) + static_cast<unsigned>(m);
+        if (bz >= nbz) break;  // the same for the whole warp
+        const unsigned bits =
+            __ballot_sync(0xffffffffu, bx < nbx && !((busy >> m) & 1u));
+        if (lane == 0 && bits) {
+            const size_t c0 = static_cast<size_t>(bz) * nbxy + row0;
+            const unsigned sh = static_cast<unsigned>(c0 & 31u);
+            atomicOr(fr + (c0 >> 5), bits << sh);
+            // the spill-over holds bits of real bricks only when nonzero (so
+            // the word lies inside the mask)
+            if (sh && (bits >> (32u - sh))) atomicOr(fr + (c0 >> 5) + 1, bits >> (32u - sh));
+        }
+    }
 }
 
 __global__ void export_kernel(const void* __restrict__ data, int storage, OutLayout L, int nx,
@@ -283,11 +300,13 @@ cudaError_t launch_field(const float* rho, int nx, int ny, int nz, float K, hh_v
         count_launch(2);
     }
     if (masks) {
-        const size_t cells = static_cast<size_t>(vol->ncx) * vol->ncy * vol->ncz;
-        const unsigned blocks = static_cast<unsigned>((cells + 255) / 256);
-        free_mask_kernel<<<blocks, 256, 0, s>>>(vol->colbits_dev, pitch, ny + 2, runs, vol->ncx,
-                                                vol->ncy, vol->ncz, vol->free_dev,
-                                                static_cast<unsigned>(vol->mask_words));
+        e = cudaMemsetAsync(vol->free_dev, 0, vol->mask_words * sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        const unsigned nby = vol->bxy / vol->bx;
+        const dim3 mblock(32, 8);
+        const dim3 mgrid((vol->bx + 31) / 32, (nby + 7) / 8, static_cast<unsigned>(runs));
+        free_mask_kernel<<<mgrid, mblock, 0, s>>>(vol->colbits_dev, pitch, ny + 2, runs, vol->bx,
+                                                  nby, vol->bz, vol->free_dev);
         count_launch();
     }
     return cudaGetLastError();

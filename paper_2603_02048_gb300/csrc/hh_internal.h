@@ -42,11 +42,6 @@ __host__ __device__ __forceinline__ unsigned brick2_offset(unsigned i, unsigned 
            ((j & 1u) << 1) | (i & 1u);
 }
 
-// Cells of the BRICK2 occupancy masks along an axis of n grid voxels: 4-voxel
-// cells of the padded axis (n + 2 voxels with the halo).
-__host__ __device__ __forceinline__ unsigned occ_cells(int n) {
-    return static_cast<unsigned>((n + 2 + 3) / 4);
-}
 
 struct hh_volume_s {
     int nx, ny, nz;
@@ -56,14 +51,15 @@ struct hh_volume_s {
     float h_kernel;
     void* data;         // float4 (FP32) or ushort4 of halves (FP16) per voxel
     size_t bytes;       // bytes of data (BRICK2: halo of one voxel, axes padded to even)
-    // BRICK2 free-cell mask, one bit per 4^3 cell of padded lattice indices
-    // (x fastest), at data + bytes in the same allocation: cell c is free when
-    // the cells c + {0,1}^3 hold no stored nonzero voxel, so that every sample
-    // whose first corner lies in c reads eight zeros. Null for LINEAR volumes.
-    unsigned ncx, ncy, ncz;
+    // BRICK2 free-brick mask, one bit per brick in the bricks' own order (bit
+    // b & 31 of word b >> 5 for brick b), at data + bytes in the same
+    // allocation: brick B is free when the bricks B + {0,1}^3 hold no stored
+    // nonzero voxel, so that every sample whose first corner lies in B reads
+    // eight zeros. Null for LINEAR volumes.
+    unsigned bz;           // bricks along z
     size_t mask_words;     // 32-bit words of the mask
     unsigned* free_dev;
-    uint8_t* colbits_dev;  // scratch of the mask build: a byte per stored column and z run
+    uint16_t* colbits_dev; // scratch of the mask build: 16 bits per stored column and z run
     float* scales_dev;  // [2] = {s_n, s_g} on the device (1, 1 for FP32)
     unsigned* max_dev;  // [2] = bit patterns of max|dn|, max|g| (FP16 build)
     float* rho_dev;     // density scratch for particle builds (nullable)

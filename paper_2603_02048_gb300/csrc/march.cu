@@ -28,7 +28,7 @@
 // 2x2x2 micro-bricks (BRICK2) with a one-voxel halo of edge copies: the
 // bricks spread the distinct voxels of a warp's corner load over all L1 bank
 // groups, and the halo lets a sample in the box skip every index clamp.
-// A sample whose eight corners are all zero (its first corner in a free cell
+// A sample whose eight corners are all zero (its first corner in a free brick
 // of the volume's mask, built with the volume) is read as zero from one bit
 // of that mask instead of eight brick loads; every step is still taken, so
 // the results are the same bit for bit.
@@ -63,8 +63,7 @@ struct VolArgs {
     int nx, ny, nz;
     unsigned bx, bxy;   // BRICK2 bricks along x and per xy plane
     unsigned by8, bz8;  // BRICK2 strides (in elements) of one brick step in y and z
-    unsigned ncx, ncxy; // free-cell mask: 4^3 cells along x and per xy plane
-    unsigned long long mask_off;  // bytes from a volume's data to its free-cell mask
+    unsigned long long mask_off;  // bytes from a volume's data to its free-brick mask
     float bias;         // power of two above every coordinate and step
     float bias_u;       // bias - 1/2: (hi - bias_u) + lo is the lattice coordinate
     float ux, uy, uz;   // n + 1/2: the far faces in lattice coordinates
@@ -242,26 +241,24 @@ __device__ __forceinline__ Sample fetch(const VolArgs& A, const void* __restrict
 #else
     (void)flags;
 #endif
-    // A sample whose first corner lies in a free cell reads eight zeros (all
-    // eight corners lie in the cell or its +1 neighbours): it is the zero
-    // sample, read from the volume's free-cell mask instead of the bricks.
+    // BRICK2 element of corner (ix, iy, iz): brick b >> 3, slot b & 7.
+    const unsigned b = brick2_offset(ix, iy, iz, A.bx, A.bxy);
+    // A sample whose first corner lies in a free brick reads eight zeros (all
+    // eight corners lie in the brick or its +1 neighbours): it is the zero
+    // sample, read from the volume's free-brick mask (bit (b >> 3) & 31 of
+    // word b >> 8) instead of the bricks.
     {
-        const unsigned cell = (static_cast<unsigned>(iz) >> 2) * A.ncxy +
-                              (static_cast<unsigned>(iy) >> 2) * A.ncx +
-                              (static_cast<unsigned>(ix) >> 2);
         const unsigned* fm =
             reinterpret_cast<const unsigned*>(static_cast<const char*>(vol) + A.mask_off);
-        if ((__ldg(fm + (cell >> 5)) >> (cell & 31u)) & 1u) {
+        if ((__ldg(fm + (b >> 8)) >> ((b >> 3) & 31u)) & 1u) {
             Sample z;
             z.dn = z.gx = z.gy = z.gz = 0.0f;
             return z;
         }
     }
-    // BRICK2 element of corner (ix, iy, iz), then the steps to the other
-    // corners: +1 in x stays in the brick (slot +1) when ix is even, else it
-    // moves to the next brick (slot -1, brick +1: +7); likewise y (+2 or
-    // by8 - 2) and z (+4 or bz8 - 4).
-    const unsigned b = brick2_offset(ix, iy, iz, A.bx, A.bxy);
+    // The steps to the other corners: +1 in x stays in the brick (slot +1)
+    // when ix is even, else it moves to the next brick (slot -1, brick +1:
+    // +7); likewise y (+2 or by8 - 2) and z (+4 or bz8 - 4).
     const unsigned dx = (ix & 1) ? 7u : 1u;
     const unsigned dy = (iy & 1) ? A.by8 - 2u : 2u;
     const unsigned dz = (iz & 1) ? A.bz8 - 4u : 4u;
@@ -1143,8 +1140,6 @@ VolArgs make_vol_args(const hh_volume_s* vol, const hh_step_params& P, const hh_
     A.bxy = vol->bxy;
     A.by8 = vol->bx * 8u;
     A.bz8 = vol->bxy * 8u;
-    A.ncx = vol->ncx;
-    A.ncxy = vol->ncx * vol->ncy;
     A.mask_off = vol->bytes;
     // bias: a power of two B with B >= 2 * step and B >= extent + step + 1, so
     // positions in [-step, extent + step] keep hi in [B/2, 2B - 1] and both
