@@ -150,21 +150,21 @@ hh_status new_volume(const hh_grid* g, hh_volume* out) {
     const size_t padded = static_cast<size_t>(v->bxy) * brick2_count(g->nz) * 8;
     v->bytes = padded * (g->storage == HH_STORE_FP32 ? 16 : 8);
     v->bz = brick2_count(g->nz);
-    v->mask_words = (static_cast<size_t>(v->bxy) * v->bz + 31) / 32;
-    // the free-brick mask and its build scratch (16 bits per stored column
+    v->mask_words = (padded + 31) / 32;  // one bit per element (8 per brick, a byte)
+    // the free-corner mask and its build scratch (a word per stored column
     // and 16-slice z run, rows padded to 4 columns) follow the data in the
     // same allocation (the data's size is a multiple of 64 bytes, so the mask
     // is aligned); all of it starts zero: even-padding voxels read as 0, and
-    // no brick is marked free before the first build
+    // no element is marked free before the first build
     const size_t colbytes = static_cast<size_t>((g->nx + 2 + 3) & ~3) * (g->ny + 2) *
-                            ((g->nz + 15) / 16) * sizeof(uint16_t);
+                            ((g->nz + 15) / 16) * sizeof(uint32_t);
     const size_t total = v->bytes + v->mask_words * sizeof(unsigned) + colbytes;
     cudaGetDevice(&v->device);
     cudaError_t e = dev_alloc(&v->data, total);
     if (e == cudaSuccess) e = cudaMemset(v->data, 0, total);
     if (e == cudaSuccess) {
         v->free_dev = reinterpret_cast<unsigned*>(static_cast<char*>(v->data) + v->bytes);
-        v->colbits_dev = reinterpret_cast<uint16_t*>(v->free_dev + v->mask_words);
+        v->colbits_dev = reinterpret_cast<uint32_t*>(v->free_dev + v->mask_words);
     }
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void**>(&v->scales_dev), 2 * sizeof(float));
     if (e == cudaSuccess) e = dev_alloc(reinterpret_cast<void**>(&v->max_dev), 2 * sizeof(unsigned));

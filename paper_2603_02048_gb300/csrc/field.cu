@@ -17,12 +17,13 @@
 // 32-byte sectors. The volume stores are marked evict-first (st.global.cs):
 // the volume outgrows L2 anyway, and this keeps the density, which the
 // kernel is still reading, resident in L2 instead.
-// BRICK2 builds also leave the volume's free-brick mask (the march skips the
+// BRICK2 builds also leave the volume's free-corner mask (the march skips the
 // eight loads of a sample whose corners are all zero): the store pass records
-// per column and run which z bricks (pairs of padded slices) hold a nonzero
-// stored voxel (16 bits, no atomics), and free_mask_kernel turns those into
-// one bit per brick. The store passes walk their runs unrolled by 2, not 4:
-// with the column's bits to carry, 4 spilled and was slower.
+// per column and run which slices hold a nonzero stored voxel (a 32-bit word,
+// no atomics), and free_mask_kernel turns those into one bit per stored
+// voxel, set when the eight voxels of the cell it is the first corner of are
+// all zero. The store passes walk their runs unrolled by 2, not 4: with the
+// column's bits to carry, 4 spilled and was slower.
 #include "hh_internal.h"
 
 namespace hh {
@@ -35,7 +36,7 @@ struct Cell {
 struct OutLayout {
     int layout;
     unsigned bx, bxy;
-    uint16_t* colbits;    // BRICK2: per stored (padded) column and z run, the z bricks
+    uint32_t* colbits;    // BRICK2: per stored (padded) column and z run, the slices
                           // where it stored a nonzero voxel (null: none); rows of
                           // `pitch` columns
     int pitch;
@@ -153,23 +154,13 @@ __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __res
         }
     }
     if (OCC && L.colbits && J < Hh) {
-        // 16 bits per stored column and run (no atomics), bit m for padded z
-        // brick (k0 >> 1) + m: k0 is a multiple of 16, so slice k0 + t (padded
-        // k0 + t + 1) lies in brick offset (t + 1) >> 1 (t = 0 -> 0, 1-2 -> 1,
-        // ..., 13-14 -> 7, 15 -> 8): bit 0 is slice bit 0 and bit m >= 1 the
-        // OR of slice bits 2m - 1 and 2m, i.e. the odd bits of
-        // nzk | (nzk >> 1), gathered. The halo slice 0 shares slice 0's
-        // brick, and the halo slice nz + 1, a copy of slice nz - 1 = k0 + t',
-        // lies in brick offset (t' + 2) >> 1.
-        static_assert(FIELD_ZRUN == 16, "brick offsets assume 16-slice runs");
-        unsigned odd = ((nzk | (nzk >> 1)) >> 1) & 0x5555u;  // bit 2i: slices 2i + 1, 2i + 2
-        odd = (odd | (odd >> 1)) & 0x3333u;
-        odd = (odd | (odd >> 2)) & 0x0F0Fu;
-        odd = (odd | (odd >> 4)) & 0x00FFu;                   // bit i: brick offset i + 1
-        unsigned zbits = (odd << 1) | (nzk & 1u);
-        if (k1 == nz && ((nzk >> (nz - 1 - k0)) & 1u)) zbits |= 1u << ((nz + 1 - k0) >> 1);
-        L.colbits[(static_cast<size_t>(blockIdx.y) * Hh + J) * L.pitch + I] =
-            static_cast<uint16_t>(zbits);
+        // one word per stored column and run (no atomics): bit t for grid
+        // slice k0 + t (padded k0 + t + 1), and in the last run bit nz - k0
+        // (at most 16) for the halo slice nz + 1, a copy of slice nz - 1; the
+        // halo slice 0, a copy of slice 0, is bit 0 of the first run
+        unsigned bits = nzk;
+        if (k1 == nz) bits |= ((nzk >> (nz - 1 - k0)) & 1u) << (nz - k0);
+        L.colbits[(static_cast<size_t>(blockIdx.y) * Hh + J) * L.pitch + I] = bits;
     }
     if (MODE == 1) {  // block maximum, then one atomic per block
         for (int o = 16; o > 0; o >>= 1) {
@@ -193,58 +184,72 @@ __global__ void __launch_bounds__(256, 8) field_column_kernel(const float* __res
     }
 }
 
-// The free-brick mask from the store pass's column bits. Brick B = (bx, by,
-// bz) of padded indices is free when none of the bricks B + {0,1}^3 (the
-// eight corners of any sample whose first corner lies in B are in them)
-// holds a stored nonzero voxel. A thread takes the 4x4 columns x in
-// 2bx .. 2bx + 3, y in 2by .. 2by + 3 (the 16-bit entries of two columns 2c,
-// 2c + 1 are one aligned 32-bit word; rows are padded to 4 columns, the
-// padding never written, so zero) and runs r and r + 1: run r's bits cover
-// z bricks 8r .. 8r + 8 and run r + 1's 8r + 8 .. 8r + 16, so their OR
-// gives the occupancy of z bricks 8r + 1 .. 8r + 9 in full (and of brick 0
-// for r = 0), hence the bits of bricks bz = 8r + 1 .. 8r + 8 (and 0). A warp
-// is 32 consecutive bx: for each bz its 32 bits are consecutive in the mask
-// (bricks in their own order, x fastest) and are ORed into the two words
-// they straddle; the mask is cleared before.
-__global__ void free_mask_kernel(const uint16_t* __restrict__ colbits, int pitch, int H, int runs,
+// The free-corner mask from the store pass's column words: one bit per
+// stored element of the BRICK2 layout (bit b & 7 of byte b >> 3 for element
+// b, i.e. a byte per brick, bit = slot), set when the voxel at padded (I, J,
+// K) and its +1 neighbours on each axis (the eight corners of the trilinear
+// cell whose first corner it is) hold no stored nonzero value. A thread takes
+// the bricks (bx, by, bz) of one brick column (bx, by) whose slices lie in
+// run r: bz = 8r + 1 .. 8r + 8 (padded slices 16r + 2 .. 16r + 17), and bz =
+// 0 too when r = 0. It reads the column words of the 3 x 3 stored columns
+// I = 2bx .. 2bx + 2, J = 2by .. 2by + 2 for runs r and r + 1 (zero beyond the
+// stored columns and runs), shifted so that bit j stands for padded slice
+// 16r + j (bit 0 only needed for r = 0: the halo slice 0), ORs neighbouring
+// columns and rows for the four (x, y) slot parities and neighbouring slices
+// for z, and stores each brick's byte (one writer per byte, no atomics).
+__global__ void free_mask_kernel(const uint32_t* __restrict__ colbits, int pitch, int H, int runs,
                                  unsigned nbx, unsigned nby, unsigned nbz,
-                                 unsigned* __restrict__ fr) {
+                                 uint8_t* __restrict__ fr) {
     const unsigned bx = blockIdx.x * 32 + threadIdx.x;
     const unsigned by = blockIdx.y * blockDim.y + threadIdx.y;
     const int r = static_cast<int>(blockIdx.z);
-    if (by >= nby) return;  // whole warps: threadIdx.y is one warp's
-    unsigned occ = 0;       // bit m: z brick 8r + m holds a nonzero voxel (m = 0 .. 16)
-    if (bx < nbx) {
-        const bool two_words = 2 * bx + 2 < static_cast<unsigned>(pitch);
-        const int j1 = min(2 * static_cast<int>(by) + 4, H);
-        for (int q = 0; q < 2 && r + q < runs; ++q) {
-            unsigned v = 0;
-            for (int J = 2 * static_cast<int>(by); J < j1; ++J) {
-                const unsigned* row = reinterpret_cast<const unsigned*>(
-                    colbits + (static_cast<size_t>(r + q) * H + J) * pitch + 2 * bx);
-                v |= __ldg(row);
-                if (two_words) v |= __ldg(row + 1);
+    if (bx >= nbx || by >= nby) return;
+    unsigned xo[3][2];  // per row: columns (2bx, 2bx+1) and (2bx+1, 2bx+2) ORed
+#pragma unroll
+    for (int jr = 0; jr < 3; ++jr) {
+        const int J = 2 * static_cast<int>(by) + jr;
+        unsigned c[3] = {0u, 0u, 0u};
+        if (J < H) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (r + q >= runs) break;
+                const uint32_t* row = colbits + (static_cast<size_t>(r + q) * H + J) * pitch;
+#pragma unroll
+                for (int ic = 0; ic < 3; ++ic) {
+                    const unsigned I = 2 * bx + static_cast<unsigned>(ic);
+                    if (I < static_cast<unsigned>(pitch)) {
+                        const unsigned w = __ldg(row + I);
+                        // run r: bit t -> padded 16r + 1 + t; run r + 1: 16r + 17 + t
+                        c[ic] |= q == 0 ? (w << 1) | (r == 0 ? (w & 1u) : 0u) : (w << 17);
+                    }
+                }
             }
-            occ |= ((v | (v >> 16)) & 0x1FFu) << (8 * q);
         }
+        xo[jr][0] = c[0] | c[1];
+        xo[jr][1] = c[1] | c[2];
     }
-    const unsigned busy = occ | (occ >> 1);  // bit m: brick 8r + m or 8r + m + 1 occupied
-    const unsigned lane = threadIdx.x;
-    const unsigned row0 = by * nbx + blockIdx.x * 32;  // mask bit of lane 0, less bz * nbxy
-    const unsigned nbxy = nbx * nby;
+    unsigned busy[2][2];  // [y parity][x parity]: bit j, slice 16r + j or 16r + j + 1 occupied
+#pragma unroll
+    for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+        for (int sx = 0; sx < 2; ++sx) {
+            const unsigned o = xo[sy][sx] | xo[sy + 1][sx];
+            busy[sy][sx] = o | (o >> 1);
+        }
+    const size_t nbxy = static_cast<size_t>(nbx) * nby;
+    const size_t col = static_cast<size_t>(by) * nbx + bx;
     for (int m = (r == 0) ? 0 : 1; m <= 8; ++m) {
         const unsigned bz = 8u * static_cast<unsigned>(r) + static_cast<unsigned>(m);
-        if (bz >= nbz) break;  // the same for the whole warp
-        const unsigned bits =
-            __ballot_sync(0xffffffffu, bx < nbx && !((busy >> m) & 1u));
-        if (lane == 0 && bits) {
-            const size_t c0 = static_cast<size_t>(bz) * nbxy + row0;
-            const unsigned sh = static_cast<unsigned>(c0 & 31u);
-            atomicOr(fr + (c0 >> 5), bits << sh);
-            // the spill-over holds bits of real bricks only when nonzero (so
-            // the word lies inside the mask)
-            if (sh && (bits >> (32u - sh))) atomicOr(fr + (c0 >> 5) + 1, bits >> (32u - sh));
-        }
+        if (bz >= nbz) break;
+        unsigned byte = 0;
+#pragma unroll
+        for (int sz = 0; sz < 2; ++sz)
+#pragma unroll
+            for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+                for (int sx = 0; sx < 2; ++sx)
+                    byte |= ((~busy[sy][sx] >> (2 * m + sz)) & 1u) << (sx | (sy << 1) | (sz << 2));
+        fr[bz * nbxy + col] = static_cast<uint8_t>(byte);
     }
 }
 
@@ -300,13 +305,12 @@ cudaError_t launch_field(const float* rho, int nx, int ny, int nz, float K, hh_v
         count_launch(2);
     }
     if (masks) {
-        e = cudaMemsetAsync(vol->free_dev, 0, vol->mask_words * sizeof(unsigned), s);
-        if (e != cudaSuccess) return e;
         const unsigned nby = vol->bxy / vol->bx;
         const dim3 mblock(32, 8);
         const dim3 mgrid((vol->bx + 31) / 32, (nby + 7) / 8, static_cast<unsigned>(runs));
         free_mask_kernel<<<mgrid, mblock, 0, s>>>(vol->colbits_dev, pitch, ny + 2, runs, vol->bx,
-                                                  nby, vol->bz, vol->free_dev);
+                                                  nby, vol->bz,
+                                                  reinterpret_cast<uint8_t*>(vol->free_dev));
         count_launch();
     }
     return cudaGetLastError();

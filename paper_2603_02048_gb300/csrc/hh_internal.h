@@ -51,15 +51,15 @@ struct hh_volume_s {
     float h_kernel;
     void* data;         // float4 (FP32) or ushort4 of halves (FP16) per voxel
     size_t bytes;       // bytes of data (BRICK2: halo of one voxel, axes padded to even)
-    // BRICK2 free-brick mask, one bit per brick in the bricks' own order (bit
-    // b & 31 of word b >> 5 for brick b), at data + bytes in the same
-    // allocation: brick B is free when the bricks B + {0,1}^3 hold no stored
-    // nonzero voxel, so that every sample whose first corner lies in B reads
-    // eight zeros. Null for LINEAR volumes.
+    // BRICK2 free-corner mask, one bit per stored element in the layout's own
+    // order (bit b & 31 of word b >> 5 for element b), at data + bytes in the
+    // same allocation: set when the element's voxel and its +1 neighbours on
+    // each axis hold no stored nonzero value, so that a sample whose first
+    // corner is that voxel reads eight zeros. Null for LINEAR volumes.
     unsigned bz;           // bricks along z
     size_t mask_words;     // 32-bit words of the mask
     unsigned* free_dev;
-    uint16_t* colbits_dev; // scratch of the mask build: 16 bits per stored column and z run
+    uint32_t* colbits_dev; // scratch of the mask build: a word per stored column and z run
     float* scales_dev;  // [2] = {s_n, s_g} on the device (1, 1 for FP32)
     unsigned* max_dev;  // [2] = bit patterns of max|dn|, max|g| (FP16 build)
     float* rho_dev;     // density scratch for particle builds (nullable)

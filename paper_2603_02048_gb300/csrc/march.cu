@@ -28,9 +28,9 @@
 // 2x2x2 micro-bricks (BRICK2) with a one-voxel halo of edge copies: the
 // bricks spread the distinct voxels of a warp's corner load over all L1 bank
 // groups, and the halo lets a sample in the box skip every index clamp.
-// A sample whose eight corners are all zero (its first corner in a free brick
-// of the volume's mask, built with the volume) is read as zero from one bit
-// of that mask instead of eight brick loads; every step is still taken, so
+// A sample whose eight corners are all zero (its first corner marked in the
+// volume's free-corner mask, built with the volume) is read as zero from one
+// bit of that mask instead of eight brick loads; every step is still taken, so
 // the results are the same bit for bit.
 #include <algorithm>
 #include <cmath>
@@ -63,7 +63,7 @@ struct VolArgs {
     int nx, ny, nz;
     unsigned bx, bxy;   // BRICK2 bricks along x and per xy plane
     unsigned by8, bz8;  // BRICK2 strides (in elements) of one brick step in y and z
-    unsigned long long mask_off;  // bytes from a volume's data to its free-brick mask
+    unsigned long long mask_off;  // bytes from a volume's data to its free-corner mask
     float bias;         // power of two above every coordinate and step
     float bias_u;       // bias - 1/2: (hi - bias_u) + lo is the lattice coordinate
     float ux, uy, uz;   // n + 1/2: the far faces in lattice coordinates
@@ -243,14 +243,14 @@ __device__ __forceinline__ Sample fetch(const VolArgs& A, const void* __restrict
 #endif
     // BRICK2 element of corner (ix, iy, iz): brick b >> 3, slot b & 7.
     const unsigned b = brick2_offset(ix, iy, iz, A.bx, A.bxy);
-    // A sample whose first corner lies in a free brick reads eight zeros (all
-    // eight corners lie in the brick or its +1 neighbours): it is the zero
-    // sample, read from the volume's free-brick mask (bit (b >> 3) & 31 of
-    // word b >> 8) instead of the bricks.
+    // A sample whose eight corners are all zero is the zero sample: read from
+    // the volume's free-corner mask (bit b & 31 of word b >> 5; the funnel
+    // shift takes the shift count mod 32) instead of the bricks.
     {
         const unsigned* fm =
             reinterpret_cast<const unsigned*>(static_cast<const char*>(vol) + A.mask_off);
-        if ((__ldg(fm + (b >> 8)) >> ((b >> 3) & 31u)) & 1u) {
+        const unsigned w = __ldg(fm + (b >> 5));
+        if (__funnelshift_r(w, w, b) & 1u) {
             Sample z;
             z.dn = z.gx = z.gy = z.gz = 0.0f;
             return z;

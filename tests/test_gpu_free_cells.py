@@ -1,12 +1,12 @@
-"""The march's free-brick skip on fields built to catch a wrong skip.
+"""The march's free-space skip on fields built to catch a wrong skip.
 
-A volume's free-brick mask marks the 2^3 bricks of padded lattice indices
-whose samples read eight zero corners; the march takes such a sample as zero
-without reading the bricks. Here the field is zero except at single voxels
-with strong values, placed on the edges of the bricks (padded indices 1-5, 7,
-8), at the grid's faces (whose halo copies sit in the first and last bricks),
-in the last, partial bricks of ragged grids and on both sides of the 16-slice
-runs the mask is built from. A nonzero sample taken for
+A volume's free-corner mask marks the voxels (padded lattice indices) that
+are the first corner of a trilinear cell whose eight corners are all zero;
+the march takes a sample in such a cell as zero without reading the bricks.
+Here the field is zero except at single voxels with strong values, placed on
+the edges of the 2^3 micro-bricks (padded indices 1-5, 7, 8), at the grid's
+faces (whose halo copies are stored too), in the last, partial bricks of
+ragged grids and on both sides of the 16-slice runs the mask is built from. A nonzero sample taken for
 zero would turn a passing ray by about 1e-3 rad, a thousand times the
 tolerance, so every ray is held to the oracle with no excusal (fixed steps,
 where the march is well conditioned), from several sides, on FP32 and FP16
