@@ -231,9 +231,9 @@ hh_status hh_volume_export(hh_volume vol, float* dst_dev, void* stream);
 
 /* Grid, FP16 scales (1 for FP32 storage) and device bytes of a volume's
  * packed field (bookkeeping; no paper passage; the same allocation also holds
- * a free-brick mask, one bit per 2x2x2 voxels, and its build scratch, 16 bits
- * per stored column and 16 slices: under 2 % more). Synchronises `stream` to
- * read the scales. Any output may be NULL. */
+ * a free-corner mask, one bit per voxel, and its build scratch, a word per
+ * stored column and 16 slices: under 5 % more). Synchronises `stream` to read
+ * the scales. Any output may be NULL. */
 hh_status hh_volume_info(hh_volume vol, hh_grid* grid, float* s_n, float* s_g, size_t* bytes,
                          void* stream);
 
