@@ -105,9 +105,15 @@ __device__ __forceinline__ float3 operator-(float3 a, float3 b) {
 __device__ __forceinline__ float3 operator*(float s, float3 a) {
     return make_float3(s * a.x, s * a.y, s * a.z);
 }
-__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// Sums of products are written with explicit FMAs: a plain a * b + c * d lets
+// the compiler fuse either product, and which one it fuses follows the
+// surrounding code, so results would change with unrelated edits.
+__device__ __forceinline__ float dot(float3 a, float3 b) {
+    return fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x));
+}
 __device__ __forceinline__ float3 cross(float3 a, float3 b) {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    return make_float3(fmaf(a.y, b.z, -(a.z * b.y)), fmaf(a.z, b.x, -(a.x * b.z)),
+                       fmaf(a.x, b.y, -(a.y * b.x)));
 }
 __device__ __forceinline__ float3 normalized(float3 v) {
     const float len = sqrtf(dot(v, v));
@@ -219,9 +225,11 @@ __device__ __forceinline__ float4 ld_fp16(const ushort4* __restrict__ v, unsigne
 __device__ unsigned long long g_bounds_violations;
 #endif
 
+// Returns false, leaving s unset, for a sample whose eight corners are all
+// zero (the zero sample).
 template <int STORAGE, bool CLAMP>
-__device__ __forceinline__ Sample fetch(const VolArgs& A, const void* __restrict__ vol, float3 u,
-                                        uint32_t& flags) {
+__device__ __forceinline__ bool fetch_nonzero(const VolArgs& A, const void* __restrict__ vol,
+                                              float3 u, uint32_t& flags, Sample& s) {
     int ix, iy, iz;
     float fx, fy, fz;
     axis_cell<CLAMP>(u.x, A.nx, ix, fx);
@@ -250,11 +258,7 @@ __device__ __forceinline__ Sample fetch(const VolArgs& A, const void* __restrict
         const unsigned* fm =
             reinterpret_cast<const unsigned*>(static_cast<const char*>(vol) + A.mask_off);
         const unsigned w = __ldg(fm + (b >> 5));
-        if (__funnelshift_r(w, w, b) & 1u) {
-            Sample z;
-            z.dn = z.gx = z.gy = z.gz = 0.0f;
-            return z;
-        }
+        if (__funnelshift_r(w, w, b) & 1u) return false;
     }
     // The steps to the other corners: +1 in x stays in the brick (slot +1)
     // when ix is even, else it moves to the next brick (slot -1, brick +1:
@@ -315,12 +319,19 @@ __device__ __forceinline__ Sample fetch(const VolArgs& A, const void* __restrict
     }
     // FP16 storage: the sample stays in code units (value / scale); the
     // power-of-two scales are applied downstream, where a product by them is
-    // exact, so the result equals scaling here (see perp_rate)
-    Sample s;
+    // exact, so the result equals scaling here (see perp_of)
     s.dn = c.x;
     s.gx = c.y;
     s.gy = c.z;
     s.gz = c.w;
+    return true;
+}
+
+template <int STORAGE, bool CLAMP>
+__device__ __forceinline__ Sample fetch(const VolArgs& A, const void* __restrict__ vol, float3 u,
+                                        uint32_t& flags) {
+    Sample s;
+    if (!fetch_nonzero<STORAGE, CLAMP>(A, vol, u, flags, s)) s.dn = s.gx = s.gy = s.gz = 0.0f;
     return s;
 }
 
@@ -352,7 +363,7 @@ __device__ __forceinline__ float3 renormalize(float3 w1, float3 d1) {
 // v clamps; value / 255).
 __device__ __forceinline__ float3 environment(const VolArgs& A, float3 d) {
     const float phi = atan2f(d.y, d.x);
-    const float theta = atan2f(sqrtf(d.x * d.x + d.y * d.y), d.z);
+    const float theta = atan2f(sqrtf(fmaf(d.y, d.y, d.x * d.x)), d.z);
     const float W = static_cast<float>(A.bgW), H = static_cast<float>(A.bgH);
     const float u = fmaf(phi, W / (2.0f * kPi), 0.5f * W - 0.5f);
     float v = fmaf(theta, H / kPi, -0.5f);
@@ -500,17 +511,21 @@ __device__ __forceinline__ float exit_fraction(const VolArgs& A, float3 hi, floa
 // and s_g are powers of two, so every such product is exact and the results
 // equal those of scaling the sample first: n = 1 + dn s_n is one rounding
 // either way, and |g_perp| = s_g |g_perp / s_g| exactly.
-template <int STORAGE, bool CLAMP>
-__device__ __forceinline__ float3 perp_rate(const VolArgs& A, const void* __restrict__ vol,
-                                            float3 u, float3 w, float s_n, float s_g, float& n,
-                                            float& gperp_norm, uint32_t& flags) {
-    const Sample s = fetch<STORAGE, CLAMP>(A, vol, u, flags);
+template <int STORAGE>
+__device__ __forceinline__ float3 perp_of(const Sample& s, float3 w, float s_n, float s_g,
+                                          float& n, float& gperp_norm) {
     n = STORAGE == HH_STORE_FP32 ? 1.0f + s.dn : fmaf(s.dn, s_n, 1.0f);
     const float3 g = make_float3(s.gx, s.gy, s.gz);
     const float3 gp = fma3(-dot(w, g), w, g);
     gperp_norm = sqrt_approx(dot(gp, gp));
     if (STORAGE != HH_STORE_FP32) gperp_norm *= s_g;
     return gp;
+}
+template <int STORAGE, bool CLAMP>
+__device__ __forceinline__ float3 perp_rate(const VolArgs& A, const void* __restrict__ vol,
+                                            float3 u, float3 w, float s_n, float s_g, float& n,
+                                            float& gperp_norm, uint32_t& flags) {
+    return perp_of<STORAGE>(fetch<STORAGE, CLAMP>(A, vol, u, flags), w, s_n, s_g, n, gperp_norm);
 }
 
 // Per-ray state of the march: primary direction w_ref, deflection d, biased
@@ -522,6 +537,7 @@ struct RayState {
     int k;
     uint32_t flags;
     float sn, sg;  // the volume's FP16 scales, read once per ray
+    float ds0;     // the step length at a zero sample (n = 1, |g_perp| = 0)
 };
 
 // Pixel (x, y) of slot p (0..31) of a tile_w x (32 / tile_w) warp tile. Each
@@ -538,11 +554,13 @@ __device__ __forceinline__ void tile_pixel(int p, int tile_w_log2, int& x, int& 
 }
 
 // Ray generation and slab entry (flags = HIT when the ray enters the box).
+template <bool ADAPTIVE>
 __device__ __forceinline__ void ray_begin(const VolArgs& V, const float* __restrict__ scales,
                                           const ViewArgs& C, int px, int py, RayState& R) {
     R.wr = primary_ray(C, px, py);
     R.sn = __ldg(scales);
     R.sg = __ldg(scales + 1);
+    R.ds0 = step_length<ADAPTIVE>(V, 1.0f, 0.0f);
     R.k = 0;
     R.flags = 0;
     R.d = make_float3(0.0f, 0.0f, 0.0f);
@@ -599,17 +617,33 @@ __device__ __forceinline__ bool ray_step(const VolArgs& V, const void* __restric
         const float3 gp4 = perp_rate<STORAGE, true>(V, vol, fma3(ds, w3, C), w4, R.sn, R.sg, n4,
                                                     unused, R.flags);
         const float3 k4 = (__fdividef(1.0f, n4) * gsc) * gp4;
-        const float3 ksum = k1 + 2.0f * (k2 + k3) + k4;
+        // k1 + 2 (k2 + k3) + k4 (every k is a product: the adds are kept
+        // unfused, __fadd_rn, so no product is folded into them)
+        const float3 ksum =
+            make_float3(__fadd_rn(fmaf(2.0f, __fadd_rn(k2.x, k3.x), k1.x), k4.x),
+                        __fadd_rn(fmaf(2.0f, __fadd_rn(k2.y, k3.y), k1.y), k4.y),
+                        __fadd_rn(fmaf(2.0f, __fadd_rn(k2.z, k3.z), k1.z), k4.z));
         const float3 dsum = fma3(ds * (1.0f / 6.0f), ksum, d);
         dnew = renormalize(wr + dsum, dsum);
         const float3 dpos = (1.0f / 6.0f) * (d + 2.0f * (d2 + d3) + d4);
         inc = ds * (wr + dpos);
     } else {
-        float n, gpn;
-        const float3 w = wr + d;
-        const float3 gp = perp_rate<STORAGE, false>(V, vol, C, w, R.sn, R.sg, n, gpn, R.flags);
-        ds = step_length<ADAPTIVE>(V, n, gpn);
-        const float3 d1 = fma3(__fdividef(ds, n) * gsc, gp, d);
+        Sample smp;
+        float3 d1;
+        if (fetch_nonzero<STORAGE, false>(V, vol, C, R.flags, smp)) {
+            float n, gpn;
+            const float3 gp = perp_of<STORAGE>(smp, wr + d, R.sn, R.sg, n, gpn);
+            ds = step_length<ADAPTIVE>(V, n, gpn);
+            d1 = fma3(__fdividef(ds, n) * gsc, gp, d);
+        } else {
+            // the zero sample: n = 1 and g_perp = 0 exactly, so the branch
+            // above would give the step length ds0 (the same operations on
+            // the same operands) and d1 = d + 0 = d (d is never -0: it starts
+            // at +0 and a sum that rounds to zero is +0); a warp whose lanes
+            // all sample zero skips the g_perp and Eq. 18 arithmetic
+            ds = R.ds0;
+            d1 = d;
+        }
         // Eq. 16: w' = normalize(w1), C' = C + ds w'; with w' = (1 + r) w1
         // the increment is ds (1 + r) w1 (w' itself is formed only at the exit)
         const float3 w1 = wr + d1;
@@ -700,7 +734,7 @@ __global__ void __launch_bounds__(128, (STEPPER == HH_STEP_RK4) ? 6 : HH_MARCH_M
     if (px >= C.W || py >= C.H) return;
     RayState R;
     float3 ep = C.eye, ed = C.eye;
-    ray_begin(V, V.scales, C, px, py, R);
+    ray_begin<ADAPTIVE>(V, V.scales, C, px, py, R);
     if (R.flags & HH_FLAG_HIT)
         while (R.k < V.max_steps && !ray_step<STORAGE, STEPPER, ADAPTIVE>(V, V.vol, R, ep, ed)) {
         }
@@ -784,7 +818,7 @@ __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_M
             if (px < C.W && py < C.H) {
                 RayState R;
                 float3 ep = make_float3(0.0f, 0.0f, 0.0f), ed = ep;
-                ray_begin(V, V.scales, C, px, py, R);
+                ray_begin<ADAPTIVE>(V, V.scales, C, px, py, R);
                 if (R.flags & HH_FLAG_HIT)
                     while (R.k < V.max_steps && !ray_step<STORAGE, STEPPER, ADAPTIVE>(V, V.vol, R, ep, ed)) {
                     }
@@ -827,7 +861,7 @@ __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_BATCH_M
                     py = ty * (32 >> tile_w_log2) + ly;
                     vi = tile_view;
                     if (px < C.W && py < C.H) {
-                        ray_begin(V, V.scales, C, px, py, R);
+                        ray_begin<ADAPTIVE>(V, V.scales, C, px, py, R);
                         if ((R.flags & HH_FLAG_HIT) && V.max_steps > 0) have = true;
                         else ray_end(V, C, px, py, R, ep, ed);
                     }
@@ -1028,7 +1062,7 @@ __global__ void __launch_bounds__(256, (STEPPER == HH_STEP_RK4) ? 3 : HH_WORKER_
         if (px < C.W && py < C.H) {
             RayState R;
             float3 ep = make_float3(0.0f, 0.0f, 0.0f), ed = ep;
-            ray_begin(V, jscales, C, px, py, R);
+            ray_begin<ADAPTIVE>(V, jscales, C, px, py, R);
             if (R.flags & HH_FLAG_HIT)
                 while (R.k < V.max_steps && !ray_step<STORAGE, STEPPER, ADAPTIVE>(V, jvol, R, ep, ed)) {
                 }
