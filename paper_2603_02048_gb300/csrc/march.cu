@@ -30,8 +30,11 @@
 // groups, and the halo lets a sample in the box skip every index clamp.
 // A sample whose eight corners are all zero (its first corner marked in the
 // volume's free-corner mask, built with the volume) is read as zero from one
-// bit of that mask instead of eight brick loads; every step is still taken, so
-// the results are the same bit for bit.
+// bit of that mask instead of eight brick loads, and the Eq. 16 step then
+// takes n = 1, g_perp = 0 and their step length without the arithmetic (a
+// warp whose lanes all sample zero skips it); every step is still taken with
+// the values the general branch would compute, so the results do not depend
+// on the skip.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
