@@ -210,13 +210,6 @@ __device__ __forceinline__ float4 xlerp_fp16(uint2 a, uint2 b, float2 tt) {
     return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
-__device__ __forceinline__ float4 ld_fp16(const ushort4* __restrict__ v, unsigned i) {
-    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(v) + i);
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
-    return make_float4(a.x, a.y, b.x, b.y);
-}
-
 // Trilinear sample of {dn, g} at lattice coordinate u = position + 1/2
 // (Sec. 3.3.1: n and grad n sampled with trilinear interpolation); FP16
 // volumes are interpolated as stored (code units, value / scale).
