@@ -33,6 +33,7 @@
 #include <thread>
 #include <vector>
 
+#include "admission.h"
 #include "hh_internal.h"
 #include "pool.h"
 
@@ -401,14 +402,13 @@ void hh_server_s::reset_queue() {
 void hh_server_s::admit() {
     const double t = now_ms();
     // smallest request first, except that a request waiting longer than
-    // kAgeMs goes ahead of every younger one (oldest first among them)
+    // kAgeMs goes ahead of every younger one (oldest first among them);
+    // tickets no longer known (released or cancelled) go last
     std::stable_sort(pending.begin(), pending.end(), [&](uint64_t a, uint64_t b) {
         auto ia = reqs.find(a), ib = reqs.find(b);
         if (ia == reqs.end() || ib == reqs.end()) return ia != reqs.end() && ib == reqs.end();
-        const bool oa = t - ia->second.t_submit > kAgeMs, ob = t - ib->second.t_submit > kAgeMs;
-        if (oa != ob) return oa;
-        if (oa) return ia->second.t_submit < ib->second.t_submit;
-        return ia->second.rays < ib->second.rays;
+        return hh::admit_before({ia->second.t_submit, ia->second.rays},
+                                {ib->second.t_submit, ib->second.rays}, t, kAgeMs);
     });
     for (auto it = pending.begin(); it != pending.end();) {
         auto rit = reqs.find(*it);
